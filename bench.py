@@ -1,0 +1,382 @@
+"""Benchmark of the HEOM-2DVS hot path on GB300 (one JSON line on rank 0).
+
+Metric: HEOM ADO-updates/s (one ADO of one branch advanced by one full RK4
+step) and the derived 2D spectra/hour, for the mixed-precision and plain FP64
+GPU paths.
+
+A timed "step" is one sample period of the t3 phase of the 2D scan over the
+whole batched branch set of the workload: m RK4 steps of all 2*n1 branches
+(rephasing + non-rephasing) x all ADOs, then the FP64 trace of every branch.
+This is the loop that carries >99% of a spectrum's work; the remaining rows of
+the path (equilibration, kicks, t1 trunk, t2, 2D DFT) run inside the e2e
+measurement, which calls the public C ABI (heom_response_2d_rows) on a block of
+t1 rows with the equilibrium state uploaded from pinned host memory each step.
+
+--impl reference times the FP64 CPU oracle (tests' reference implementation)
+on the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+WORKLOADS = {
+    # name: (config, precision code, e2e rows per step)
+    "c3-mixed": ("c3", 2, 16),
+    "c3-fp32": ("c3", 1, 16),
+    "c2-fp64": ("c2", 0, 2),
+    "c3-fp64": ("c3", 0, 2),
+    "c1-fp64": ("c1", 0, 64),
+}
+PREC_NAME = {0: "f64", 1: "f32", 2: "bf16x3-f32"}
+
+
+def describe(cfg, model, grid, d, nado):
+    return {"workload": "%s: %d-mode MAB, d=%d, %d ADOs (L=%d), %dx%d t1xt3, t2=%s fs, dt=%g fs, m=%d"
+            % (cfg, len(model["modes"]), d, nado, model["depth_L"], grid["n1"], grid["n3"],
+               grid["t2_fs"], grid["dt_fs"], grid["steps_per_sample"]),
+            "branches": 2 * grid["n1"], "d": d, "n_ado": nado}
+
+
+def ado_updates_per_spectrum(grid, nado, n_t2_index=0):
+    """ADO-updates of one full spectrum (one t2): trunk + t2 + t3 for both pathways."""
+    n1, n3, m = grid["n1"], grid["n3"], grid["steps_per_sample"]
+    t2 = sorted(grid["t2_fs"])[n_t2_index]
+    n2 = int(round(t2 / grid["dt_fs"]))
+    B = 2 * n1
+    return nado * ((n1 - 1) * m + B * n2 + B * (n3 - 1) * m)
+
+
+def rows_ado_updates(grid, nado, j0, j1):
+    m, n3 = grid["steps_per_sample"], grid["n3"]
+    B = 2 * (j1 - j0)
+    n2 = max(int(round(t / grid["dt_fs"])) for t in grid["t2_fs"])
+    return nado * ((j1 - 1) * m + B * n2 + len(grid["t2_fs"]) * B * (n3 - 1) * m)
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic cost per ADO-update of the fused stage kernel
+# ---------------------------------------------------------------------------
+def algorithmic_costs(model, d, nado, ado_table, nb_counts, prec):
+    """flops and bytes of one ADO-update (4 Horner stages), averaged over the ADOs.
+
+    flops per stage: [H, w] with real H: 2 real-times-complex d^3 products = 8 d^3;
+    per mode s: neighbour sums (8 d^2 per coupling entry) and V_s applied to A_s, B_s
+    from both sides (16 d^2 n_s); decay and update (8 d^2).
+    bytes per ADO-update: 11 state passes (stage 1 reads y and writes w, stages 2-4
+    read w, y and write) of d^2 complex.
+    """
+    dims = [md["n_levels"] for md in model["modes"]]
+    avg_nb = nb_counts.sum(axis=0) / nado   # per mode
+    stage = 8.0 * d ** 3 + 8.0 * d * d
+    for s, n in enumerate(dims):
+        stage += 8.0 * d * d * avg_nb[s] + (16.0 * d * d * n if avg_nb[s] > 0 else 0.0)
+    flops = 4.0 * stage
+    b = 16.0 if prec == 0 else 8.0
+    return flops, 11.0 * d * d * b
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def oracle_sample(cfg, budget_s=12.0, max_steps=50):
+    """Time oracle RK4 steps of one branch of the workload (FP64, host cores)."""
+    from oracle import heom as OH
+    from oracle import model as OM
+    model, grid = W.config(cfg)
+    prob = OM.Problem(model)
+    rng = np.random.default_rng(3)
+    x = (rng.standard_normal((1, prob.nado, prob.d, prob.d))
+         + 1j * rng.standard_normal((1, prob.nado, prob.d, prob.d))) * 1e-3
+    t0 = time.perf_counter()
+    steps = 0
+    while steps < max_steps:
+        x = OH.rk4_step(prob, x, grid["dt_fs"])
+        steps += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": steps * prob.nado / dt, "unit": "ADO-updates/s", "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": "%d FP64 RK4 step(s) of one branch (%d ADOs, d=%d) of %s, numpy/BLAS on %d "
+                      "host threads" % (steps, prob.nado, prob.d, cfg, os.cpu_count()),
+            "seconds": dt}
+
+
+def run_reference(args, cfg, rank, world):
+    if rank != 0:
+        return
+    vals = []
+    t_all = time.perf_counter()
+    for i in range(args.warmup + args.steps):
+        r = oracle_sample(cfg, budget_s=max(2.0, 30.0 / (args.warmup + args.steps)), max_steps=20)
+        if i >= args.warmup:
+            vals.append(r)
+    value = float(np.mean([v["value"] for v in vals]))
+    model, grid = W.config(cfg)
+    line = {"impl": "reference", "metric": "HEOM ADO-updates/s (2D spectra/hour derived)",
+            "value": value, "unit": "ADO-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean([v["seconds"] for v in vals])),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded water-like MAB model)",
+            "config": {"workload": cfg + " (oracle sample: one branch)"},
+            "cpu_baseline": {"value": value, "unit": "ADO-updates/s", "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": vals[0]["sample"]},
+            "e2e": {"value": value, "unit": "ADO-updates/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_all}
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="c2-fp64", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    cfg, prec, e2e_rows = WORKLOADS[args.workload]
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, cfg, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2601_20550_gb300 import heom as H
+
+    model, grid = W.config(cfg)
+    h = H.heom_build_hierarchy(model, prec)
+    d, nado = h.d, h.n_ado
+    eq = H.heom_equilibrate(h, grid["dt_fs"], grid["t_eq_fs"], 0.0)
+    m = grid["steps_per_sample"]
+    B = 2 * grid["n1"]
+    cdt = torch.complex128 if prec == 0 else torch.complex64
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+    # batched t3 state: every branch starts from mu_plus^x rho_eq (the third kick)
+    eqB = H.heom_state_create(h, B, prec)
+    H.heom_state_broadcast(eq, eqB)
+    y = torch.empty((B, nado, d, d), dtype=cdt, device=dev)
+    H.heom_kick_dev(h, H.heom_state_device_ptr(eqB), y.data_ptr(), B, prec, 1, sp)
+    torch.cuda.synchronize()
+    del eqB
+    wa = torch.empty_like(y)
+    wb = torch.empty_like(y)
+    traces = torch.zeros((args.warmup + args.steps, B), dtype=torch.complex128, device=dev)
+    torch.cuda.synchronize()
+
+    ops = H.heom_get_operators(h)
+    nb = np.zeros((nado, len(model["modes"])))
+    bath = ops["bath"]
+    ado = ops["ado"]
+    for i in range(nado):
+        for j in range(h.n_exp):
+            s = int(bath[j, 0])
+            nb[i, s] += (ado[i, j] > 0)
+            nb[i, s] += (ado[i].sum() < model["depth_L"])
+    flops_upd, bytes_upd = algorithmic_costs(model, d, nado, ado, nb, prec)
+
+    def one_step(i, ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        H.heom_propagate_dev(h, y.data_ptr(), wa.data_ptr(), wb.data_ptr(), B, prec,
+                             grid["dt_fs"], m, sp)
+        if ev is not None:
+            ev[1].record(stream)
+        H.heom_trace_dev(h, y.data_ptr(), B, prec, 3, traces[i].data_ptr(), sp)
+
+    for i in range(args.warmup):
+        one_step(i)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    n_launch0 = H.heom_launch_count()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for i in range(args.steps):
+        one_step(args.warmup + i, evs[i])
+    stop.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches = H.heom_launch_count() - n_launch0
+    clocks = clk.stop()
+    t_ms = start.elapsed_time(stop)
+    prop_ms = sum(a.elapsed_time(b) for a, b in evs)
+    if dist:
+        t = torch.tensor([t_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+    if not torch.isfinite(traces.real).all():
+        raise RuntimeError("non-finite traces in the timed region")
+    units = float(B) * nado * m * args.steps * world
+    value = units / (t_ms / 1000.0)
+    per_spec = ado_updates_per_spectrum(grid, nado)
+    stage_launches = 4 * m * args.steps
+    stage_s = prop_ms / 1000.0 / stage_launches
+    per_launch_units = B * nado / 4.0       # one stage = a quarter of an ADO-update per ADO
+    peaks, peak_kind = measured_peaks()
+    if prec == 0:
+        achieved = flops_upd * per_launch_units / stage_s / 1e12
+        peak = 1.25
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s)",
+                "algorithmic_flops_per_ado_update": flops_upd}
+    else:
+        achieved = bytes_upd * per_launch_units / stage_s / 1e9
+        peak = peaks["hbm_gbs"]
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_kind,
+                "algorithmic_bytes_per_ado_update": bytes_upd,
+                "flops_TFLOPs": flops_upd * per_launch_units / stage_s / 1e12}
+
+    # ---------------- e2e through the public C ABI with host buffers ----------------
+    e2e = None
+    if not args.no_e2e:
+        eq_host = H.heom_state_download(eq)
+        pinned = torch.from_numpy(eq_host.view(np.float64)).pin_memory()
+        eq_up = H.heom_state_create(h, 1, 0)
+        rows = min(e2e_rows, grid["n1"])
+        # warm-up call on one row
+        H.heom_response_2d_rows(h, eq, grid, 0, 1)
+        tt = []
+        d2h = 0
+        for i in range(args.e2e_steps):
+            j0 = (i * rows) % grid["n1"]
+            j1 = min(grid["n1"], j0 + rows)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            H.lib().heom_state_upload(eq_up.h, H._P(pinned.data_ptr()))
+            RI, RII = H.heom_response_2d_rows(h, eq_up, grid, j0, j1)
+            tt.append((time.perf_counter() - t0, rows_ado_updates(grid, nado, j0, j1)))
+            d2h = RI.nbytes + RII.nbytes
+        e2e = {"value": sum(u for _, u in tt) / sum(s for s, _ in tt), "unit": "ADO-updates/s",
+               "h2d_bytes_per_step": int(pinned.numel() * 8), "d2h_bytes_per_step": int(d2h),
+               "call": "heom_state_upload + heom_response_2d_rows (%d t1 rows, both pathways, all "
+                       "t3 and t2, trunk recomputed)" % rows,
+               "seconds_per_step": sum(s for s, _ in tt) / len(tt)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_sample(cfg, budget_s=15.0, max_steps=30)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        conf = describe(cfg, model, grid, d, nado)
+        conf.update({"parallelism": "replicas" if world > 1 else "single-gpu",
+                     "l2": "inputs larger than L2 (state %.1f GB)" % (y.numel() * y.element_size() / 1e9),
+                     "precision": PREC_NAME[prec]})
+        line = {
+            "metric": "HEOM ADO-updates/s (2D spectra/hour derived)",
+            "value": value, "unit": "ADO-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAME[prec],
+            "data": "synthetic (seeded water-like MAB model; no dataset)",
+            "config": conf,
+            "spectra_per_hour": 3600.0 * value / per_spec,
+            "ado_updates_per_spectrum": per_spec,
+            "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+            "gpu_launches": int(launches),
+        }
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,245 @@
+/*
+ * heom2dvs.h - C ABI of the GB300 HEOM-2DVS hot path.
+ *
+ * The library propagates the hierarchical equations of motion (HEOM) of the
+ * multi-mode anharmonic Brownian (MAB) model with fourth-order Runge-Kutta and
+ * builds the third-order response R(t3, t2, t1) and the 2D correlation IR
+ * spectrum (Hoshino and Tanimura, arXiv 2601.20550, Sec. II).  All propagation,
+ * kicks, traces and Fourier sums run in CUDA kernels for sm_103a; the host only
+ * builds the (small) operator matrices and index tables.
+ *
+ * Conventions shared by every entry point
+ *   - hbar = 1; time in fs; model energies in cm^-1 (converted inside).
+ *   - Complex numbers cross the ABI as interleaved (re, im) pairs of double.
+ *   - Matrices are row-major.  The product basis orders modes with mode 0 the
+ *     slowest index.  A state holds, per branch, every ADO in canonical order
+ *     (ascending by (sum of the multi-index, the multi-index as a tuple)), each
+ *     ADO a d x d matrix: host layout [branch][ado][d][d] complex.
+ *   - Every call returns a heom_status; no exception or abort crosses the ABI.
+ *     On failure heom_last_error() gives a message (thread-local).
+ *   - The caller owns descriptors and host arrays; the library owns handles and
+ *     their device memory.  A handle must not be used by two threads at once.
+ *   - Host-pointer calls synchronise before returning.  *_dev calls take device
+ *     pointers and a cudaStream_t (passed as void*) and do not synchronise.
+ */
+#ifndef HEOM2DVS_H
+#define HEOM2DVS_H
+
+#include <stdint.h>
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HEOM_OK = 0,
+  HEOM_EINVAL = -1,     /* invalid argument or descriptor */
+  HEOM_ENOMEM = -2,     /* device or host allocation failed */
+  HEOM_ECUDA = -3,      /* CUDA runtime error (message has the CUDA string) */
+  HEOM_EUNSTABLE = -4,  /* dt outside the RK4 stability region of the Liouvillian */
+  HEOM_ETIMEOUT = -5,   /* a bounded device wait ran out */
+  HEOM_ENOTCONV = -6,   /* equilibrium tolerance not reached by t_max */
+  HEOM_ENONFINITE = -7, /* a trace or residual became NaN/Inf */
+  HEOM_ECKPT = -8       /* checkpoint integrity failure */
+} heom_status;
+
+/* Arithmetic of the propagation.  The equilibrium hierarchy is always FP64. */
+typedef enum {
+  HEOM_FP64 = 0,        /* complex128 state, FP64 right-hand side */
+  HEOM_FP32 = 1,        /* complex64 state, FP32 right-hand side (CUDA cores) */
+  HEOM_BF16X3 = 2       /* complex64 state, split-BF16 tensor-core products, FP32 accumulation */
+} heom_precision;
+
+/*
+ * One vibrational mode s (Sec. II.A, Eqs. System Hamiltonian, Potentials,
+ * counter Hamiltonian, h_int, NLdip; Drude bath Eq. drude; Pade order Sec. II.B).
+ *   potential  0: omega (p^2 + q^2)/2 + g3 q^3 / 6 in a harmonic basis of n_prim states
+ *              1: omega p^2 / 2 + D (1 - exp(-a q))^2, a = sqrt(omega/(2 D)), on a
+ *                 uniform sinc-DVR grid of n_prim points spanning [q_min, q_max]
+ *   q is dimensionless with mass m_s = 1/omega_s.
+ *   n_levels   eigenstates kept (the mode's basis size n_s)
+ *   zeta_cm, gamma_cm  Drude parameters; reorganisation energy m zeta gamma / 2
+ *   V_LL, V_SL system-bath coupling V_s(q) = V_LL q + V_SL q^2 / 2
+ *   mu1, mu2   dipole mu_s q_s + mu_ss q_s^2 / 2
+ *   K_pade     number of Pade terms K_s (the mode has K_s + 1 exponentials)
+ */
+typedef struct {
+  int potential;
+  double omega_cm, g3_cm, morse_D_cm;
+  int n_levels, n_prim;
+  double q_min, q_max;
+  double zeta_cm, gamma_cm, V_LL, V_SL, mu1, mu2;
+  int K_pade;
+} heom_mode;
+
+/* Mode-mode coupling g q_s q_t + (g_s2t q_s^2 q_t + g_st2 q_s q_t^2)/6 and the
+ * dipole cross term mu_st q_s q_t (Eqs. Potential ss', NLdip).  s != t. */
+typedef struct {
+  int s, t;
+  double g_st_cm, g_s2t_cm, g_st2_cm, mu_st;
+} heom_pair;
+
+/* The model (Eqs. Total Hamiltonian .. h_int) plus hierarchy depth L (all ADOs
+ * with sum(n) <= L; Sec. II.B after Eq. HEOM_DB) and the propagation precision. */
+typedef struct {
+  int n_modes;
+  const heom_mode *modes;
+  int n_pairs;
+  const heom_pair *pairs;
+  double T_K;
+  int depth_L;
+  int precision;   /* heom_precision */
+} heom_model;
+
+/* 2D time grid: t1 = j m dt (j < n1), t3 = k m dt (k < n3), t2 from t2_fs[n_t2]
+ * (each a multiple of dt).  m = steps_per_sample. */
+typedef struct {
+  double dt_fs;
+  int steps_per_sample, n1, n3, n_t2;
+  const double *t2_fs;
+} heom_grid;
+
+typedef struct heom_hier heom_hier;     /* opaque, library-owned */
+typedef struct heom_state heom_state;   /* opaque, library-owned */
+
+typedef struct {
+  int d;            /* product-basis dimension */
+  int n_ado;        /* number of ADOs */
+  int n_exp;        /* exponentials D = sum_s (K_s + 1) */
+  int n_modes;
+  int precision;
+  double beta;      /* 1/kT in fs/rad */
+} heom_hier_info;
+
+/*
+ * Build the model matrices and the hierarchy (Sec. II.A-B): mode eigenbases,
+ * H_S' with counter terms, V_s, mu and its raising part, the Pade/Matsubara
+ * bath exponentials (Eqs. L1, L2, Pade1, Pade2) and the ADO neighbour tables,
+ * then upload them.  *out receives a new handle (free with heom_free_hier).
+ * Errors: HEOM_EINVAL (bad descriptor), HEOM_ENOMEM, HEOM_ECUDA.
+ */
+heom_status heom_build_hierarchy(const heom_model *m, heom_hier **out);
+heom_status heom_get_info(const heom_hier *h, heom_hier_info *info);
+
+/*
+ * Copy the model operators to host arrays (for inspection and tests):
+ * H [d*d], mu [d*d], mu_plus [d*d] (may be NULL), bath [n_exp*4] as
+ * (mode, nu, Re c, Im c) with C(t) = sum_j c_j exp(-nu_j t), ado [n_ado*n_exp]
+ * multi-indices (may be NULL).
+ */
+heom_status heom_get_operators(const heom_hier *h, double *H, double *mu, double *mu_plus,
+                               double *bath, int32_t *ado);
+
+/* Per-mode data of mode s: energies [n_s] and q^k matrices qk [4][n_s][n_s] (k = 1..4)
+ * in the kept eigenbasis (may be NULL). */
+heom_status heom_get_mode(const heom_hier *h, int s, double *energies, double *qk);
+
+/*
+ * Equilibrium hierarchy (Sec. II.C.1): rho_0 = |0><0| (product ground state), all
+ * other ADOs zero, propagated with FP64 RK4.  tol <= 0: exactly round(t_max/dt)
+ * steps.  tol > 0: stop when max_n ||RHS(rho)_n||_F <= tol ||rho_0||_F (checked
+ * every 100 steps); HEOM_ENOTCONV if t_max is reached first (the state is still
+ * returned).  *rho_eq receives a new FP64 single-branch state.
+ */
+heom_status heom_equilibrate(heom_hier *h, double dt_fs, double t_max_fs, double tol,
+                             heom_state **rho_eq);
+
+/* States: create (zeroed), upload/download host arrays [branches][n_ado][d][d]
+ * complex (interleaved doubles; FP32 states are converted). */
+heom_status heom_state_create(const heom_hier *h, int branches, int precision, heom_state **out);
+heom_status heom_state_upload(heom_state *s, const double *host);
+heom_status heom_state_download(const heom_state *s, double *host);
+int heom_state_branches(const heom_state *s);
+
+/*
+ * Advance every branch of rho by n_steps RK4 steps of Eq. HEOM_DB (Sec. III).
+ * The RK4 polynomial is evaluated in nested (Horner) form, identical to the
+ * classic four-stage tableau for this linear, time-independent equation.
+ * Errors: HEOM_EINVAL, HEOM_EUNSTABLE (dt fails the stability pre-check),
+ * HEOM_ECUDA.
+ */
+heom_status heom_propagate(heom_hier *h, heom_state *rho, double dt_fs, int64_t n_steps);
+
+/*
+ * Apply the hyperoperator K^x (K = mu, mu_plus or mu_minus: which = 0, 1, 2) to
+ * every ADO of every branch in place (the dipole kicks of Sec. II.C).
+ */
+heom_status heom_kick(heom_hier *h, heom_state *rho, int which);
+
+/* i^order tr{mu rho_0} of every branch into out [branches] complex (Eqs. R1, RFTIRI). */
+heom_status heom_trace(heom_hier *h, const heom_state *rho, int order, double *out);
+
+/*
+ * Third-order response and 2D correlation spectrum (Sec. II.C.2, Eqs. RFTIRI,
+ * echo, virtual-echo, 2D-rephasing, 2D-nonrephasing, correlation-spectrum):
+ *   R_I  = i^3 tr{mu G(t3) (mu+)^x G(t2) (mu+)^x G(t1) (mu-)^x rho_eq}
+ *   R_II = i^3 tr{mu G(t3) (mu+)^x G(t2) (mu-)^x G(t1) (mu+)^x rho_eq}
+ * where mu+ keeps the elements of mu that raise the total excitation number
+ * and mu- = (mu+)^T.  All t1 branches of both pathways are propagated together.
+ * Outputs (caller-owned host arrays, any may be NULL):
+ *   R_I, R_II [n_t2][n1][n3] complex;  S_C [n_t2][n1][n3] double, indexed by
+ *   (Omega1 index q, Omega3 index p), Omega_p = 2 pi p / (N m dt), with the
+ *   trapezoid weights 1/2 at t = 0 and S_C(q, p) = S_R((n1 - q) mod n1, p) + S_NR(q, p).
+ * rho_eq must be a single-branch FP64 state (from heom_equilibrate).  The
+ * propagation runs in the hierarchy's precision; traces accumulate in FP64.
+ */
+heom_status heom_response_2d(heom_hier *h, const heom_state *rho_eq, const heom_grid *g,
+                             double *R_I, double *R_II, double *S_C);
+
+/*
+ * Rows j0 <= j < j1 (t1 = j m dt) of R_I and R_II only, into R_I, R_II
+ * [n_t2][j1 - j0][n3] complex (either may be NULL).  The union of row ranges is
+ * the full response; row blocks are independent (the unit of work sharding).
+ * The t1 trunk is recomputed from rho_eq up to t1 = j0 m dt.
+ */
+heom_status heom_response_2d_rows(heom_hier *h, const heom_state *rho_eq, const heom_grid *g, int j0,
+                                  int j1, double *R_I, double *R_II);
+
+/* Copy branch 0 of src into every branch of dst (converting precision). */
+heom_status heom_state_broadcast(const heom_state *src, heom_state *dst);
+
+/* Device address of a state's storage ([branches][n_ado][d][d], complex128 or
+ * complex64); valid until heom_free_state. */
+void *heom_state_device_ptr(heom_state *s);
+
+/*
+ * Linear response R1(t) = i tr{mu G(t) mu^x rho_eq} at t = k m dt, k < n (Eq. R1),
+ * into R1 [n] complex, and the absorption I(Omega_p) = Im[dtau sum_k w_k
+ * exp(+i Omega_p t_k) R1(t_k)] into I [n] (may be NULL).
+ */
+heom_status heom_response_1d(heom_hier *h, const heom_state *rho_eq, double dt_fs, int m, int n,
+                             double *R1, double *I);
+
+/*
+ * Device-pointer RK4 propagation on a caller stream: state and two scratch
+ * buffers of the same size, each [branches][n_ado][d][d] complex (complex128 for
+ * HEOM_FP64, complex64 otherwise), row-major, ADO stride d*d.  No allocation,
+ * no synchronisation; the result is in state.
+ */
+heom_status heom_propagate_dev(heom_hier *h, void *state, void *scratch_a, void *scratch_b,
+                               int branches, int precision, double dt_fs, int64_t n_steps,
+                               void *stream);
+
+/* out = K^x in for every ADO of every branch of a device state (K as in
+ * heom_kick); in and out must not overlap.  Caller stream, no synchronisation. */
+heom_status heom_kick_dev(heom_hier *h, const void *in, void *out, int branches, int precision,
+                          int which, void *stream);
+
+/* i^order tr{mu rho_0} of each branch of a device state into out (device,
+ * [branches] complex128) on a caller stream; no synchronisation. */
+heom_status heom_trace_dev(heom_hier *h, const void *state, int branches, int precision, int order,
+                           void *out, void *stream);
+
+void heom_free_hier(heom_hier *h);
+void heom_free_state(heom_state *s);
+const char *heom_last_error(void);
+
+/* Count of library kernel launches since load (monotonic; for launch accounting). */
+uint64_t heom_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEOM2DVS_H */

@@ -1,0 +1,765 @@
+// C-ABI entry points of libheom2dvs (declared in include/heom2dvs.h).
+//
+// The host code here only allocates, uploads the model built by model.cpp and
+// sequences kernel launches; every step of the propagation, the kicks, the
+// traces and the Fourier sums runs on the GPU.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "heom2dvs.h"
+#include "kernels.cuh"
+#include "model.h"
+#include "tc_stage.h"
+
+namespace heom {
+
+static thread_local std::string g_last_error;
+static std::atomic<uint64_t> g_launches{0};
+
+void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+struct Fail {
+  heom_status st;
+  std::string msg;
+};
+
+#define CUDA_TRY(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t _e = (expr);                                                             \
+    if (_e != cudaSuccess)                                                               \
+      throw Fail{HEOM_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)};       \
+  } while (0)
+
+#define LAUNCH_CHECK()                                                                   \
+  do {                                                                                   \
+    cudaError_t _e = cudaGetLastError();                                                 \
+    if (_e != cudaSuccess) throw Fail{HEOM_ECUDA, std::string("launch: ") + cudaGetErrorString(_e)}; \
+  } while (0)
+
+template <typename T>
+static T *dev_upload(const std::vector<T> &v) {
+  T *p = nullptr;
+  size_t bytes = std::max<size_t>(1, v.size() * sizeof(T));
+  if (cudaMalloc(&p, bytes) != cudaSuccess) throw Fail{HEOM_ENOMEM, "cudaMalloc failed (model tables)"};
+  if (!v.empty()) CUDA_TRY(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return p;
+}
+
+template <typename T>
+static std::vector<T> cast_vec(const std::vector<double> &v) {
+  return std::vector<T>(v.begin(), v.end());
+}
+
+struct DeviceBuffer {
+  void *p = nullptr;
+  size_t bytes = 0;
+  DeviceBuffer() = default;
+  explicit DeviceBuffer(size_t n) { alloc(n); }
+  void alloc(size_t n) {
+    release();
+    if (n == 0) n = 16;
+    if (cudaMalloc(&p, n) != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      throw Fail{HEOM_ENOMEM, "cudaMalloc of " + std::to_string(n) + " bytes failed"};
+    }
+    bytes = n;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  ~DeviceBuffer() { release(); }
+  DeviceBuffer(const DeviceBuffer &) = delete;
+  DeviceBuffer &operator=(const DeviceBuffer &) = delete;
+};
+
+static int grid_for(int64_t total) {
+  int64_t blocks = (total + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(blocks, 152LL * 64));
+}
+
+}  // namespace heom
+
+using namespace heom;
+
+struct heom_hier {
+  Model M;
+  cudaStream_t stream = nullptr;
+  // device copies
+  std::vector<void *> allocs;
+  DevModel<double> dm64{};
+  DevModel<float> dm32{};
+  double *mu64 = nullptr, *mup64 = nullptr, *mum64 = nullptr;
+  float *mu32 = nullptr, *mup32 = nullptr, *mum32 = nullptr;
+  double *mu_trace = nullptr;   // FP64 mu for traces
+  TcOperators tc{};             // tensor-core operator tiles (HEOM_BF16X3)
+  bool on_device = false;
+  ~heom_hier() {
+    for (void *p : allocs) cudaFree(p);
+    if (stream) cudaStreamDestroy(stream);
+  }
+  template <typename T>
+  T *up(const std::vector<T> &v) {
+    T *p = dev_upload(v);
+    allocs.push_back(p);
+    return p;
+  }
+};
+
+struct heom_state {
+  int branches = 0, precision = 0, d = 0, n_ado = 0;
+  DeviceBuffer buf;
+  int64_t elems() const { return (int64_t)branches * n_ado * d * d; }
+  size_t elem_bytes() const { return precision == HEOM_FP64 ? 16 : 8; }
+};
+
+namespace heom {
+
+static heom_status fail(heom_status st, const std::string &msg) {
+  g_last_error = msg;
+  return st;
+}
+
+template <typename F>
+static heom_status guarded(F &&f) {
+  try {
+    return f();
+  } catch (const Fail &e) {
+    return fail(e.st, e.msg);
+  } catch (const std::invalid_argument &e) {
+    return fail(HEOM_EINVAL, e.what());
+  } catch (const std::bad_alloc &) {
+    return fail(HEOM_ENOMEM, "host allocation failed");
+  } catch (const std::exception &e) {
+    return fail(HEOM_EINVAL, e.what());
+  }
+}
+
+template <typename R>
+static DevModel<R> &dev_model(heom_hier *h);
+template <>
+DevModel<double> &dev_model<double>(heom_hier *h) { return h->dm64; }
+template <>
+DevModel<float> &dev_model<float>(heom_hier *h) { return h->dm32; }
+
+template <typename R>
+static const R *mu_of(heom_hier *h, int which);
+template <>
+const double *mu_of<double>(heom_hier *h, int which) { return which == 0 ? h->mu64 : which == 1 ? h->mup64 : h->mum64; }
+template <>
+const float *mu_of<float>(heom_hier *h, int which) { return which == 0 ? h->mu32 : which == 1 ? h->mup32 : h->mum32; }
+
+// Necessary condition for RK4 stability: the largest Bohr frequency of H_S' and
+// the largest ADO decay rate must each lie inside the RK4 region (|z| < 2.78 on
+// the axes).  It does not bound the system-bath couplings.
+static void stability_check(heom_hier *h, double dt) {
+  if (!(dt > 0) || !std::isfinite(dt)) throw Fail{HEOM_EINVAL, "dt must be > 0"};
+  const Model &M = h->M;
+  std::vector<double> A = M.H, w, Z;
+  jacobi_eigh(A, M.d, w, Z);
+  double spread = w.back() - w.front();
+  double maxdecay = 0;
+  for (double g : M.decay) maxdecay = std::max(maxdecay, g);
+  if (dt * spread > 2.78 || dt * maxdecay > 2.78)
+    throw Fail{HEOM_EUNSTABLE, "dt outside the RK4 stability region (dt*spread(H) = " +
+                                   std::to_string(dt * spread) + ", dt*max decay = " +
+                                   std::to_string(dt * maxdecay) + ")"};
+}
+
+// One RK4 step on branches [y] with scratch wa, wb, Horner form:
+//   wa = y + dt/4 L(y); wb = y + dt/3 L(wa); wa = y + dt/2 L(wb); y = y + dt L(wa)
+template <typename R>
+static void rk4_steps(heom_hier *h, typename CxT<R>::type *y, typename CxT<R>::type *wa,
+                      typename CxT<R>::type *wb, int branches, double dt, int64_t nsteps,
+                      cudaStream_t st, int precision) {
+  const DevModel<R> &dm = dev_model<R>(h);
+  const int64_t total = (int64_t)branches * dm.n_ado * dm.d * dm.d;
+  if (total == 0 || nsteps <= 0) return;
+  if (precision == HEOM_BF16X3 && tc_supported(h->tc)) {
+    tc_rk4_steps(h->tc, (float2 *)y, (float2 *)wa, (float2 *)wb, branches, dt, nsteps, st);
+    return;
+  }
+  const int grid = grid_for(total);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    stage_kernel<R><<<grid, 256, 0, st>>>(y, y, wa, (R)(dt / 4), dm, total);
+    stage_kernel<R><<<grid, 256, 0, st>>>(wa, y, wb, (R)(dt / 3), dm, total);
+    stage_kernel<R><<<grid, 256, 0, st>>>(wb, y, wa, (R)(dt / 2), dm, total);
+    stage_kernel<R><<<grid, 256, 0, st>>>(wa, y, y, (R)dt, dm, total);
+    count_launch(4);
+  }
+  LAUNCH_CHECK();
+}
+
+template <typename R>
+static void kick_into(heom_hier *h, const typename CxT<R>::type *in, typename CxT<R>::type *out,
+                      int branches, int which, cudaStream_t st) {
+  const Model &M = h->M;
+  const int64_t total = (int64_t)branches * M.n_ado * M.d * M.d;
+  kick_kernel<R><<<grid_for(total), 256, 0, st>>>(in, out, mu_of<R>(h, which), M.d, total);
+  count_launch(1);
+  LAUNCH_CHECK();
+}
+
+template <typename R>
+static void trace_into(heom_hier *h, const typename CxT<R>::type *w, int branches, int order,
+                       double2 *out, int64_t ostride, cudaStream_t st) {
+  const Model &M = h->M;
+  trace_kernel<R><<<branches, 256, 0, st>>>(w, h->mu_trace, M.d, M.n_ado, order, out, ostride);
+  count_launch(1);
+  LAUNCH_CHECK();
+}
+
+// ---------------------------------------------------------------------------
+// 2D response (Sec. II.C.2) in precision R.
+// ---------------------------------------------------------------------------
+// Rows [jr0, jr1) of R_I and R_II into Rdev laid out [n_t2][2][jr1 - jr0][n3].
+template <typename R>
+static void response_2d_rows_impl(heom_hier *h, const heom_state *eq, const heom_grid *g, int jr0, int jr1,
+                                  double2 *Rdev) {
+  using C = typename CxT<R>::type;
+  const Model &M = h->M;
+  cudaStream_t st = h->stream;
+  const int n1 = jr1 - jr0, n3 = g->n3, m = g->steps_per_sample, nt2 = g->n_t2;
+  const double dt = g->dt_fs;
+  const int64_t per_branch = (int64_t)M.n_ado * M.d * M.d;
+  const size_t cb = sizeof(C);
+  // t2 in ascending order, as step counts
+  std::vector<int> order(nt2);
+  std::vector<int64_t> n2(nt2);
+  for (int i = 0; i < nt2; ++i) {
+    order[i] = i;
+    double r = g->t2_fs[i] / dt;
+    n2[i] = (int64_t)std::llround(r);
+    if (g->t2_fs[i] < 0 || std::fabs(r - n2[i]) > 1e-6) throw Fail{HEOM_EINVAL, "t2 must be a non-negative multiple of dt"};
+  }
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return n2[a] < n2[b]; });
+  // single-branch buffers: equilibrium (precision R), trunk and its scratch
+  DeviceBuffer eqR(per_branch * cb), T(per_branch * cb), ta(per_branch * cb), tb(per_branch * cb);
+  if (sizeof(R) == 8) {
+    CUDA_TRY(cudaMemcpyAsync(eqR.p, eq->buf.p, per_branch * cb, cudaMemcpyDeviceToDevice, st));
+  } else {
+    convert_f64_to_f32<<<grid_for(per_branch), 256, 0, st>>>((const double2 *)eq->buf.p, (float2 *)eqR.p, per_branch);
+    count_launch(1);
+    LAUNCH_CHECK();
+  }
+  // branch chunk size: both pathways of jc t1 samples, 3 or 4 state sets
+  const int nsets = nt2 > 1 ? 4 : 3;
+  size_t free_b = 0, total_b = 0;
+  CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  const double budget = 0.85 * (double)free_b;
+  int jc = n1;
+  while (jc > 1 && (double)nsets * 2 * jc * per_branch * cb > budget) jc = (jc + 1) / 2;
+  if ((double)nsets * 2 * jc * per_branch * cb > budget) throw Fail{HEOM_ENOMEM, "state does not fit in device memory"};
+  const int64_t setb = 2LL * jc * per_branch * cb;
+  DeviceBuffer P0(setb), P1(setb), P2(setb), P3(nsets == 4 ? setb : 16);
+  for (int j0 = 0; j0 < n1; j0 += jc) {
+    const int nj = std::min(jc, n1 - j0);
+    const int B = 2 * nj;
+    C *BR = (C *)P0.p;
+    // trunk: rephasing first kick, propagated to t1 = j0 m dt
+    kick_into<R>(h, (const C *)eqR.p, (C *)T.p, 1, 2, st);
+    rk4_steps<R>(h, (C *)T.p, (C *)ta.p, (C *)tb.p, 1, dt, (int64_t)(jr0 + j0) * m, st, M.precision);
+    for (int j = 0; j < nj; ++j) {
+      if (j > 0) rk4_steps<R>(h, (C *)T.p, (C *)ta.p, (C *)tb.p, 1, dt, m, st, M.precision);
+      kick2_pair_kernel<R><<<grid_for(per_branch), 256, 0, st>>>(
+          (const C *)T.p, BR + (int64_t)j * per_branch, BR + (int64_t)(nj + j) * per_branch,
+          mu_of<R>(h, 1), mu_of<R>(h, 2), M.d, per_branch);
+      count_launch(1);
+      LAUNCH_CHECK();
+    }
+    int64_t t_now = 0;
+    for (int oi = 0; oi < nt2; ++oi) {
+      const int it = order[oi];
+      C *Y = (C *)P1.p, *WA = (C *)P2.p, *WB = (C *)(nsets == 4 ? P3.p : P0.p);
+      rk4_steps<R>(h, BR, Y, WA, B, dt, n2[it] - t_now, st, M.precision);
+      t_now = n2[it];
+      kick_into<R>(h, BR, Y, B, 1, st);
+      for (int k = 0; k < n3; ++k) {
+        if (k > 0) rk4_steps<R>(h, Y, WA, WB, B, dt, m, st, M.precision);
+        for (int pw = 0; pw < 2; ++pw) {
+          double2 *base = Rdev + (int64_t)it * 2 * n1 * n3 + (int64_t)pw * n1 * n3 + (int64_t)j0 * n3 + k;
+          trace_into<R>(h, Y + (int64_t)pw * nj * per_branch, nj, 3, base, n3, st);
+        }
+      }
+    }
+  }
+}
+
+// Device set-up of a hierarchy: stream, operator and table uploads.  Runs at the
+// first call that needs the GPU, so the host-side model can be built and
+// inspected without one.
+static void ensure_device(heom_hier *h) {
+  if (h->on_device) return;
+  Model &M = h->M;
+  CUDA_TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  std::vector<double> vl;
+  DevModel<double> d64{};
+  d64.d = M.d;
+  d64.n_ado = M.n_ado;
+  d64.n_modes = M.n_modes;
+  for (int s = 0; s < M.n_modes; ++s) {
+    d64.dims[s] = M.dims[s];
+    d64.stride[s] = M.stride[s];
+    d64.vloc_off[s] = (int)vl.size();
+    vl.insert(vl.end(), M.Vloc[s].begin(), M.Vloc[s].end());
+  }
+  DevModel<float> d32{};
+  d32.d = d64.d;
+  d32.n_ado = d64.n_ado;
+  d32.n_modes = d64.n_modes;
+  std::memcpy(d32.dims, d64.dims, sizeof(d64.dims));
+  std::memcpy(d32.stride, d64.stride, sizeof(d64.stride));
+  std::memcpy(d32.vloc_off, d64.vloc_off, sizeof(d64.vloc_off));
+  d64.H = h->up(M.H);
+  d32.H = h->up(cast_vec<float>(M.H));
+  d64.vloc = h->up(vl);
+  d32.vloc = h->up(cast_vec<float>(vl));
+  d64.decay = d32.decay = h->up(M.decay);
+  d64.nb_off = d32.nb_off = h->up(M.nb_off);
+  d64.nb_idx = d32.nb_idx = h->up(M.nb_idx);
+  d64.nb_cA = h->up(M.nb_cA);
+  d64.nb_cB = h->up(M.nb_cB);
+  d32.nb_cA = h->up(cast_vec<float>(M.nb_cA));
+  d32.nb_cB = h->up(cast_vec<float>(M.nb_cB));
+  h->dm64 = d64;
+  h->dm32 = d32;
+  std::vector<double> mum((size_t)M.d * M.d);
+  for (int a = 0; a < M.d; ++a)
+    for (int b = 0; b < M.d; ++b) mum[(size_t)a * M.d + b] = M.mu_plus[(size_t)b * M.d + a];
+  h->mu64 = h->up(M.mu);
+  h->mup64 = h->up(M.mu_plus);
+  h->mum64 = h->up(mum);
+  h->mu32 = h->up(cast_vec<float>(M.mu));
+  h->mup32 = h->up(cast_vec<float>(M.mu_plus));
+  h->mum32 = h->up(cast_vec<float>(mum));
+  h->mu_trace = h->mu64;
+  if (M.precision == HEOM_BF16X3) tc_build(h->tc, M, h->dm32, h->allocs);
+  h->on_device = true;
+}
+
+}  // namespace heom
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char *heom_last_error(void) { return g_last_error.c_str(); }
+uint64_t heom_launch_count(void) { return g_launches.load(); }
+
+heom_status heom_build_hierarchy(const heom_model *m, heom_hier **out) {
+  if (!m || !out) return fail(HEOM_EINVAL, "null argument");
+  *out = nullptr;
+  return guarded([&]() -> heom_status {
+    if (m->precision < 0 || m->precision > 2) throw Fail{HEOM_EINVAL, "precision must be 0, 1 or 2"};
+    auto h = new heom_hier();
+    try {
+      h->M = build_model(*m);
+      if (h->M.n_modes > kMaxModes) throw Fail{HEOM_EINVAL, "too many modes"};
+    } catch (...) {
+      delete h;
+      throw;
+    }
+    *out = h;
+    return HEOM_OK;
+  });
+}
+
+heom_status heom_get_info(const heom_hier *h, heom_hier_info *info) {
+  if (!h || !info) return fail(HEOM_EINVAL, "null argument");
+  info->d = h->M.d;
+  info->n_ado = h->M.n_ado;
+  info->n_exp = h->M.n_exp;
+  info->n_modes = h->M.n_modes;
+  info->precision = h->M.precision;
+  info->beta = h->M.beta;
+  return HEOM_OK;
+}
+
+heom_status heom_get_operators(const heom_hier *h, double *H, double *mu, double *mu_plus, double *bath,
+                               int32_t *ado) {
+  if (!h) return fail(HEOM_EINVAL, "null handle");
+  const Model &M = h->M;
+  if (H) std::memcpy(H, M.H.data(), M.H.size() * sizeof(double));
+  if (mu) std::memcpy(mu, M.mu.data(), M.mu.size() * sizeof(double));
+  if (mu_plus) std::memcpy(mu_plus, M.mu_plus.data(), M.mu_plus.size() * sizeof(double));
+  if (bath)
+    for (int j = 0; j < M.n_exp; ++j) {
+      bath[4 * j] = M.exp_mode[j];
+      bath[4 * j + 1] = M.exp_nu[j];
+      bath[4 * j + 2] = M.exp_re[j];
+      bath[4 * j + 3] = M.exp_im[j];
+    }
+  if (ado) std::memcpy(ado, M.ado.data(), M.ado.size() * sizeof(int32_t));
+  return HEOM_OK;
+}
+
+heom_status heom_get_mode(const heom_hier *h, int s, double *energies, double *qk) {
+  if (!h || s < 0 || s >= h->M.n_modes) return fail(HEOM_EINVAL, "bad handle or mode index");
+  const ModeBasis &mb = h->M.modes[s];
+  if (energies) std::memcpy(energies, mb.E.data(), mb.n * sizeof(double));
+  if (qk)
+    for (int k = 1; k <= 4; ++k) std::memcpy(qk + (size_t)(k - 1) * mb.n * mb.n, mb.q[k].data(), (size_t)mb.n * mb.n * sizeof(double));
+  return HEOM_OK;
+}
+
+heom_status heom_state_create(const heom_hier *h, int branches, int precision, heom_state **out) {
+  if (!h || !out || branches < 1 || precision < 0 || precision > 2) return fail(HEOM_EINVAL, "bad state arguments");
+  *out = nullptr;
+  return guarded([&]() -> heom_status {
+    ensure_device(const_cast<heom_hier *>(h));
+    auto s = new heom_state();
+    s->branches = branches;
+    s->precision = precision;
+    s->d = h->M.d;
+    s->n_ado = h->M.n_ado;
+    try {
+      s->buf.alloc(s->elems() * s->elem_bytes());
+      CUDA_TRY(cudaMemset(s->buf.p, 0, s->buf.bytes));
+    } catch (...) {
+      delete s;
+      throw;
+    }
+    *out = s;
+    return HEOM_OK;
+  });
+}
+
+int heom_state_branches(const heom_state *s) { return s ? s->branches : 0; }
+
+heom_status heom_state_upload(heom_state *s, const double *host) {
+  if (!s || !host) return fail(HEOM_EINVAL, "null argument");
+  return guarded([&]() -> heom_status {
+    const int64_t n = s->elems();
+    if (s->precision == HEOM_FP64) {
+      CUDA_TRY(cudaMemcpy(s->buf.p, host, n * 16, cudaMemcpyHostToDevice));
+    } else {
+      DeviceBuffer tmp(n * 16);
+      CUDA_TRY(cudaMemcpy(tmp.p, host, n * 16, cudaMemcpyHostToDevice));
+      convert_f64_to_f32<<<grid_for(n), 256>>>((const double2 *)tmp.p, (float2 *)s->buf.p, n);
+      count_launch(1);
+      LAUNCH_CHECK();
+      CUDA_TRY(cudaDeviceSynchronize());
+    }
+    return HEOM_OK;
+  });
+}
+
+heom_status heom_state_download(const heom_state *s, double *host) {
+  if (!s || !host) return fail(HEOM_EINVAL, "null argument");
+  return guarded([&]() -> heom_status {
+    const int64_t n = s->elems();
+    if (s->precision == HEOM_FP64) {
+      CUDA_TRY(cudaMemcpy(host, s->buf.p, n * 16, cudaMemcpyDeviceToHost));
+    } else {
+      DeviceBuffer tmp(n * 16);
+      convert_f32_to_f64<<<grid_for(n), 256>>>((const float2 *)s->buf.p, (double2 *)tmp.p, n);
+      count_launch(1);
+      LAUNCH_CHECK();
+      CUDA_TRY(cudaMemcpy(host, tmp.p, n * 16, cudaMemcpyDeviceToHost));
+    }
+    return HEOM_OK;
+  });
+}
+
+heom_status heom_propagate(heom_hier *h, heom_state *rho, double dt_fs, int64_t n_steps) {
+  if (!h || !rho || n_steps < 0) return fail(HEOM_EINVAL, "bad propagate arguments");
+  if (rho->d != h->M.d || rho->n_ado != h->M.n_ado) return fail(HEOM_EINVAL, "state does not match hierarchy");
+  return guarded([&]() -> heom_status {
+    ensure_device(h);
+    stability_check(h, dt_fs);
+    const size_t bytes = rho->elems() * rho->elem_bytes();
+    DeviceBuffer a(bytes), b(bytes);
+    if (rho->precision == HEOM_FP64)
+      rk4_steps<double>(h, (double2 *)rho->buf.p, (double2 *)a.p, (double2 *)b.p, rho->branches, dt_fs, n_steps, h->stream, HEOM_FP64);
+    else
+      rk4_steps<float>(h, (float2 *)rho->buf.p, (float2 *)a.p, (float2 *)b.p, rho->branches, dt_fs, n_steps, h->stream, rho->precision);
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return HEOM_OK;
+  });
+}
+
+heom_status heom_propagate_dev(heom_hier *h, void *state, void *scratch_a, void *scratch_b, int branches,
+                               int precision, double dt_fs, int64_t n_steps, void *stream) {
+  if (!h || !state || !scratch_a || !scratch_b || branches < 1 || n_steps < 0 || precision < 0 || precision > 2)
+    return fail(HEOM_EINVAL, "bad propagate_dev arguments");
+  return guarded([&]() -> heom_status {
+    ensure_device(h);
+    stability_check(h, dt_fs);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == HEOM_FP64)
+      rk4_steps<double>(h, (double2 *)state, (double2 *)scratch_a, (double2 *)scratch_b, branches, dt_fs, n_steps, st, precision);
+    else
+      rk4_steps<float>(h, (float2 *)state, (float2 *)scratch_a, (float2 *)scratch_b, branches, dt_fs, n_steps, st, precision);
+    return HEOM_OK;
+  });
+}
+
+heom_status heom_kick(heom_hier *h, heom_state *rho, int which) {
+  if (!h || !rho || which < 0 || which > 2) return fail(HEOM_EINVAL, "bad kick arguments");
+  return guarded([&]() -> heom_status {
+    ensure_device(h);
+    const size_t bytes = rho->elems() * rho->elem_bytes();
+    DeviceBuffer tmp(bytes);
+    if (rho->precision == HEOM_FP64)
+      kick_into<double>(h, (const double2 *)rho->buf.p, (double2 *)tmp.p, rho->branches, which, h->stream);
+    else
+      kick_into<float>(h, (const float2 *)rho->buf.p, (float2 *)tmp.p, rho->branches, which, h->stream);
+    CUDA_TRY(cudaMemcpyAsync(rho->buf.p, tmp.p, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return HEOM_OK;
+  });
+}
+
+heom_status heom_trace(heom_hier *h, const heom_state *rho, int order, double *out) {
+  if (!h || !rho || !out) return fail(HEOM_EINVAL, "bad trace arguments");
+  return guarded([&]() -> heom_status {
+    ensure_device(h);
+    DeviceBuffer o((size_t)rho->branches * 16);
+    if (rho->precision == HEOM_FP64)
+      trace_into<double>(h, (const double2 *)rho->buf.p, rho->branches, order, (double2 *)o.p, 1, h->stream);
+    else
+      trace_into<float>(h, (const float2 *)rho->buf.p, rho->branches, order, (double2 *)o.p, 1, h->stream);
+    CUDA_TRY(cudaMemcpyAsync(out, o.p, (size_t)rho->branches * 16, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return HEOM_OK;
+  });
+}
+
+heom_status heom_equilibrate(heom_hier *h, double dt_fs, double t_max_fs, double tol, heom_state **rho_eq) {
+  if (!h || !rho_eq || !(t_max_fs >= 0)) return fail(HEOM_EINVAL, "bad equilibrate arguments");
+  *rho_eq = nullptr;
+  {
+    heom_status e = guarded([&]() -> heom_status {
+      ensure_device(h);
+      return HEOM_OK;
+    });
+    if (e != HEOM_OK) return e;
+  }
+  heom_state *s = nullptr;
+  heom_status st0 = heom_state_create(h, 1, HEOM_FP64, &s);
+  if (st0 != HEOM_OK) return st0;
+  heom_status rc = guarded([&]() -> heom_status {
+    stability_check(h, dt_fs);
+    const Model &M = h->M;
+    const int64_t per = (int64_t)M.n_ado * M.d * M.d;
+    double one[2] = {1.0, 0.0};
+    CUDA_TRY(cudaMemcpy(s->buf.p, one, 16, cudaMemcpyHostToDevice));   // rho_0 = |0><0|
+    DeviceBuffer a(per * 16), b(per * 16);
+    const int64_t nmax = (int64_t)std::llround(t_max_fs / dt_fs);
+    if (tol <= 0) {
+      rk4_steps<double>(h, (double2 *)s->buf.p, (double2 *)a.p, (double2 *)b.p, 1, dt_fs, nmax, h->stream, HEOM_FP64);
+      CUDA_TRY(cudaStreamSynchronize(h->stream));
+      return HEOM_OK;
+    }
+    DeviceBuffer norms((size_t)M.n_ado * 8), zero(per * 16);
+    CUDA_TRY(cudaMemset(zero.p, 0, per * 16));
+    std::vector<double> hn(M.n_ado);
+    int64_t done = 0;
+    while (done < nmax) {
+      int64_t chunk = std::min<int64_t>(100, nmax - done);
+      rk4_steps<double>(h, (double2 *)s->buf.p, (double2 *)a.p, (double2 *)b.p, 1, dt_fs, chunk, h->stream, HEOM_FP64);
+      done += chunk;
+      // residual: a = 0 + 1 * L(rho)
+      stage_kernel<double><<<grid_for(per), 256, 0, h->stream>>>((const double2 *)s->buf.p, (const double2 *)zero.p,
+                                                                  (double2 *)a.p, 1.0, h->dm64, per);
+      ado_norms_kernel<double><<<M.n_ado, 256, 0, h->stream>>>((const double2 *)a.p, (int64_t)M.d * M.d, M.n_ado, (double *)norms.p);
+      count_launch(2);
+      LAUNCH_CHECK();
+      CUDA_TRY(cudaMemcpyAsync(hn.data(), norms.p, M.n_ado * 8, cudaMemcpyDeviceToHost, h->stream));
+      CUDA_TRY(cudaStreamSynchronize(h->stream));
+      double res = 0;
+      for (double v : hn) res = std::max(res, v);
+      ado_norms_kernel<double><<<1, 256, 0, h->stream>>>((const double2 *)s->buf.p, (int64_t)M.d * M.d, 1, (double *)norms.p);
+      count_launch(1);
+      double n0 = 0;
+      CUDA_TRY(cudaMemcpyAsync(&n0, norms.p, 8, cudaMemcpyDeviceToHost, h->stream));
+      CUDA_TRY(cudaStreamSynchronize(h->stream));
+      if (!std::isfinite(res) || !std::isfinite(n0)) throw Fail{HEOM_ENONFINITE, "equilibrium residual is not finite"};
+      if (std::sqrt(res) <= tol * std::sqrt(n0)) return HEOM_OK;
+    }
+    g_last_error = "equilibrium tolerance not reached by t_max";
+    return HEOM_ENOTCONV;
+  });
+  if (rc == HEOM_OK || rc == HEOM_ENOTCONV) {
+    *rho_eq = s;
+  } else {
+    heom_free_state(s);
+  }
+  return rc;
+}
+
+static heom_status check_response_args(heom_hier *h, const heom_state *rho_eq, const heom_grid *g) {
+  if (!h || !rho_eq || !g) return fail(HEOM_EINVAL, "null argument");
+  if (g->n1 < 1 || g->n3 < 1 || g->n_t2 < 1 || !g->t2_fs || g->steps_per_sample < 1)
+    return fail(HEOM_EINVAL, "bad grid");
+  if (rho_eq->precision != HEOM_FP64 || rho_eq->branches != 1 || rho_eq->d != h->M.d || rho_eq->n_ado != h->M.n_ado)
+    return fail(HEOM_EINVAL, "rho_eq must be a single-branch FP64 state of this hierarchy");
+  return HEOM_OK;
+}
+
+static void rows_dispatch(heom_hier *h, const heom_state *rho_eq, const heom_grid *g, int j0, int j1, double2 *Rdev) {
+  if (h->M.precision == HEOM_FP64)
+    response_2d_rows_impl<double>(h, rho_eq, g, j0, j1, Rdev);
+  else
+    response_2d_rows_impl<float>(h, rho_eq, g, j0, j1, Rdev);
+}
+
+heom_status heom_response_2d(heom_hier *h, const heom_state *rho_eq, const heom_grid *g, double *R_I,
+                             double *R_II, double *S_C) {
+  heom_status a = check_response_args(h, rho_eq, g);
+  if (a != HEOM_OK) return a;
+  return guarded([&]() -> heom_status {
+    ensure_device(h);
+    stability_check(h, g->dt_fs);
+    const int n1 = g->n1, n3 = g->n3, nt2 = g->n_t2;
+    DeviceBuffer Rdev((size_t)nt2 * 2 * n1 * n3 * 16), SCdev((size_t)nt2 * n1 * n3 * 8);
+    CUDA_TRY(cudaMemsetAsync(Rdev.p, 0, Rdev.bytes, h->stream));
+    rows_dispatch(h, rho_eq, g, 0, n1, (double2 *)Rdev.p);
+    const double dtau = g->dt_fs * g->steps_per_sample;
+    for (int it = 0; it < nt2; ++it) {
+      double2 *RI = (double2 *)Rdev.p + (int64_t)it * 2 * n1 * n3;
+      dft2d_sc_kernel<<<(n1 * n3 + 255) / 256, 256, 0, h->stream>>>(RI, RI + (int64_t)n1 * n3, n1, n3, dtau,
+                                                                     (double *)SCdev.p + (int64_t)it * n1 * n3);
+      count_launch(1);
+      LAUNCH_CHECK();
+    }
+    std::vector<double> Rh((size_t)nt2 * 2 * n1 * n3 * 2);
+    CUDA_TRY(cudaMemcpyAsync(Rh.data(), Rdev.p, Rdev.bytes, cudaMemcpyDeviceToHost, h->stream));
+    if (S_C) CUDA_TRY(cudaMemcpyAsync(S_C, SCdev.p, SCdev.bytes, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const size_t blk = (size_t)n1 * n3 * 2;
+    for (int it = 0; it < nt2; ++it) {
+      if (R_I) std::memcpy(R_I + it * blk, Rh.data() + (size_t)it * 2 * blk, blk * 8);
+      if (R_II) std::memcpy(R_II + it * blk, Rh.data() + (size_t)it * 2 * blk + blk, blk * 8);
+    }
+    for (double v : Rh)
+      if (!std::isfinite(v)) throw Fail{HEOM_ENONFINITE, "response is not finite"};
+    return HEOM_OK;
+  });
+}
+
+heom_status heom_response_2d_rows(heom_hier *h, const heom_state *rho_eq, const heom_grid *g, int j0, int j1,
+                                  double *R_I, double *R_II) {
+  heom_status a = check_response_args(h, rho_eq, g);
+  if (a != HEOM_OK) return a;
+  if (j0 < 0 || j1 > g->n1 || j0 >= j1) return fail(HEOM_EINVAL, "bad row range");
+  return guarded([&]() -> heom_status {
+    ensure_device(h);
+    stability_check(h, g->dt_fs);
+    const int nr = j1 - j0, n3 = g->n3, nt2 = g->n_t2;
+    DeviceBuffer Rdev((size_t)nt2 * 2 * nr * n3 * 16);
+    CUDA_TRY(cudaMemsetAsync(Rdev.p, 0, Rdev.bytes, h->stream));
+    rows_dispatch(h, rho_eq, g, j0, j1, (double2 *)Rdev.p);
+    std::vector<double> Rh((size_t)nt2 * 2 * nr * n3 * 2);
+    CUDA_TRY(cudaMemcpyAsync(Rh.data(), Rdev.p, Rdev.bytes, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    const size_t blk = (size_t)nr * n3 * 2;
+    for (int it = 0; it < nt2; ++it) {
+      if (R_I) std::memcpy(R_I + it * blk, Rh.data() + (size_t)it * 2 * blk, blk * 8);
+      if (R_II) std::memcpy(R_II + it * blk, Rh.data() + (size_t)it * 2 * blk + blk, blk * 8);
+    }
+    for (double v : Rh)
+      if (!std::isfinite(v)) throw Fail{HEOM_ENONFINITE, "response is not finite"};
+    return HEOM_OK;
+  });
+}
+
+heom_status heom_state_broadcast(const heom_state *src, heom_state *dst) {
+  if (!src || !dst || src->d != dst->d || src->n_ado != dst->n_ado) return fail(HEOM_EINVAL, "bad broadcast arguments");
+  return guarded([&]() -> heom_status {
+    const int64_t per = (int64_t)src->n_ado * src->d * src->d;
+    for (int b = 0; b < dst->branches; ++b) {
+      char *out = (char *)dst->buf.p + (size_t)b * per * dst->elem_bytes();
+      if (src->precision == dst->precision) {
+        CUDA_TRY(cudaMemcpy(out, src->buf.p, per * src->elem_bytes(), cudaMemcpyDeviceToDevice));
+      } else if (src->precision == HEOM_FP64) {
+        convert_f64_to_f32<<<grid_for(per), 256>>>((const double2 *)src->buf.p, (float2 *)out, per);
+        count_launch(1);
+        LAUNCH_CHECK();
+      } else {
+        convert_f32_to_f64<<<grid_for(per), 256>>>((const float2 *)src->buf.p, (double2 *)out, per);
+        count_launch(1);
+        LAUNCH_CHECK();
+      }
+    }
+    CUDA_TRY(cudaDeviceSynchronize());
+    return HEOM_OK;
+  });
+}
+
+void *heom_state_device_ptr(heom_state *s) { return s ? s->buf.p : nullptr; }
+
+heom_status heom_kick_dev(heom_hier *h, const void *in, void *out, int branches, int precision, int which,
+                          void *stream) {
+  if (!h || !in || !out || in == out || branches < 1 || precision < 0 || precision > 2 || which < 0 || which > 2)
+    return fail(HEOM_EINVAL, "bad kick_dev arguments");
+  return guarded([&]() -> heom_status {
+    ensure_device(h);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == HEOM_FP64)
+      kick_into<double>(h, (const double2 *)in, (double2 *)out, branches, which, st);
+    else
+      kick_into<float>(h, (const float2 *)in, (float2 *)out, branches, which, st);
+    return HEOM_OK;
+  });
+}
+
+heom_status heom_trace_dev(heom_hier *h, const void *state, int branches, int precision, int order, void *out,
+                           void *stream) {
+  if (!h || !state || !out || branches < 1 || precision < 0 || precision > 2) return fail(HEOM_EINVAL, "bad trace_dev arguments");
+  return guarded([&]() -> heom_status {
+    ensure_device(h);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == HEOM_FP64)
+      trace_into<double>(h, (const double2 *)state, branches, order, (double2 *)out, 1, st);
+    else
+      trace_into<float>(h, (const float2 *)state, branches, order, (double2 *)out, 1, st);
+    return HEOM_OK;
+  });
+}
+
+heom_status heom_response_1d(heom_hier *h, const heom_state *rho_eq, double dt_fs, int m, int n, double *R1,
+                             double *I) {
+  if (!h || !rho_eq || !R1 || m < 1 || n < 1) return fail(HEOM_EINVAL, "bad response_1d arguments");
+  if (rho_eq->precision != HEOM_FP64 || rho_eq->branches != 1 || rho_eq->d != h->M.d)
+    return fail(HEOM_EINVAL, "rho_eq must be a single-branch FP64 state of this hierarchy");
+  return guarded([&]() -> heom_status {
+    ensure_device(h);
+    stability_check(h, dt_fs);
+    const Model &M = h->M;
+    const int64_t per = (int64_t)M.n_ado * M.d * M.d;
+    DeviceBuffer y(per * 16), a(per * 16), b(per * 16), Rd((size_t)n * 16);
+    kick_into<double>(h, (const double2 *)rho_eq->buf.p, (double2 *)y.p, 1, 0, h->stream);
+    for (int k = 0; k < n; ++k) {
+      if (k > 0) rk4_steps<double>(h, (double2 *)y.p, (double2 *)a.p, (double2 *)b.p, 1, dt_fs, m, h->stream, HEOM_FP64);
+      trace_into<double>(h, (const double2 *)y.p, 1, 1, (double2 *)Rd.p + k, 1, h->stream);
+    }
+    CUDA_TRY(cudaMemcpyAsync(R1, Rd.p, (size_t)n * 16, cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    if (I) {
+      DeviceBuffer Id((size_t)n * 8);
+      dft1d_kernel<<<(n + 127) / 128, 128, 0, h->stream>>>((const double2 *)Rd.p, n, dt_fs * m, (double *)Id.p);
+      count_launch(1);
+      LAUNCH_CHECK();
+      CUDA_TRY(cudaMemcpyAsync(I, Id.p, (size_t)n * 8, cudaMemcpyDeviceToHost, h->stream));
+      CUDA_TRY(cudaStreamSynchronize(h->stream));
+    }
+    return HEOM_OK;
+  });
+}
+
+void heom_free_hier(heom_hier *h) { delete h; }
+void heom_free_state(heom_state *s) { delete s; }
+
+}  // extern "C"

@@ -1,0 +1,57 @@
+// Non-template kernels: 2D Fourier sums / correlation spectrum and state conversion.
+#include "kernels.cuh"
+
+namespace heom {
+
+__global__ void dft2d_sc_kernel(const double2 *__restrict__ RI, const double2 *__restrict__ RII,
+                                int n1, int n3, double dtau, double *__restrict__ SC) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= n1 * n3) return;
+  const int q = idx / n3, p = idx % n3;
+  const int qf = (n1 - q) % n1;   // -Omega1 for the rephasing part
+  double sr = 0, snr = 0;         // imaginary parts only
+  for (int j = 0; j < n1; ++j) {
+    const double wj = j == 0 ? 0.5 : 1.0;
+    double s1r, c1r, s1n, c1n;
+    sincospi(2.0 * (double)((long long)qf * j % n1) / n1, &s1r, &c1r);
+    sincospi(2.0 * (double)((long long)q * j % n1) / n1, &s1n, &c1n);
+    for (int k = 0; k < n3; ++k) {
+      const double w = wj * (k == 0 ? 0.5 : 1.0);
+      double s3, c3;
+      sincospi(2.0 * (double)((long long)p * k % n3) / n3, &s3, &c3);
+      const double2 a = RI[(long long)j * n3 + k];
+      const double2 b = RII[(long long)j * n3 + k];
+      // Im[(cos + i sin)(x + i y)] = sin x + cos y, phase = phase1 + phase3
+      const double cr = c1r * c3 - s1r * s3, sr_ = s1r * c3 + c1r * s3;
+      const double cn = c1n * c3 - s1n * s3, sn = s1n * c3 + c1n * s3;
+      sr += w * (sr_ * a.x + cr * a.y);
+      snr += w * (sn * b.x + cn * b.y);
+    }
+  }
+  SC[idx] = dtau * dtau * (sr + snr);
+}
+
+__global__ void dft1d_kernel(const double2 *__restrict__ R, int n, double dtau, double *__restrict__ I) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double s = 0;
+  for (int k = 0; k < n; ++k) {
+    double sn, cs;
+    sincospi(2.0 * (double)((long long)p * k % n) / n, &sn, &cs);
+    const double w = k == 0 ? 0.5 : 1.0;
+    s += w * (sn * R[k].x + cs * R[k].y);
+  }
+  I[p] = dtau * s;
+}
+
+__global__ void convert_f64_to_f32(const double2 *__restrict__ x, float2 *__restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = make_float2((float)x[i].x, (float)x[i].y);
+}
+
+__global__ void convert_f32_to_f64(const float2 *__restrict__ x, double2 *__restrict__ y, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = make_double2((double)x[i].x, (double)x[i].y);
+}
+
+}  // namespace heom

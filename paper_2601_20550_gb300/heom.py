@@ -1,0 +1,313 @@
+"""ctypes binding of libheom2dvs (argument marshalling only).
+
+Every function here forwards to the C entry point of the same name in
+include/heom2dvs.h; all arithmetic of the method runs in the library's CUDA
+kernels.  The library is loaded from this package directory and its absence is
+an error: there is no CPU fallback.
+"""
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libheom2dvs.so")
+
+FP64, FP32, BF16X3 = 0, 1, 2
+STATUS = {0: "HEOM_OK", -1: "HEOM_EINVAL", -2: "HEOM_ENOMEM", -3: "HEOM_ECUDA",
+          -4: "HEOM_EUNSTABLE", -5: "HEOM_ETIMEOUT", -6: "HEOM_ENOTCONV",
+          -7: "HEOM_ENONFINITE", -8: "HEOM_ECKPT"}
+
+
+class HeomError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS.get(status, status), msg))
+        self.status = status
+
+
+class heom_mode(ct.Structure):
+    _fields_ = [("potential", ct.c_int), ("omega_cm", ct.c_double), ("g3_cm", ct.c_double),
+                ("morse_D_cm", ct.c_double), ("n_levels", ct.c_int), ("n_prim", ct.c_int),
+                ("q_min", ct.c_double), ("q_max", ct.c_double), ("zeta_cm", ct.c_double),
+                ("gamma_cm", ct.c_double), ("V_LL", ct.c_double), ("V_SL", ct.c_double),
+                ("mu1", ct.c_double), ("mu2", ct.c_double), ("K_pade", ct.c_int)]
+
+
+class heom_pair(ct.Structure):
+    _fields_ = [("s", ct.c_int), ("t", ct.c_int), ("g_st_cm", ct.c_double),
+                ("g_s2t_cm", ct.c_double), ("g_st2_cm", ct.c_double), ("mu_st", ct.c_double)]
+
+
+class heom_model(ct.Structure):
+    _fields_ = [("n_modes", ct.c_int), ("modes", ct.POINTER(heom_mode)), ("n_pairs", ct.c_int),
+                ("pairs", ct.POINTER(heom_pair)), ("T_K", ct.c_double), ("depth_L", ct.c_int),
+                ("precision", ct.c_int)]
+
+
+class heom_grid(ct.Structure):
+    _fields_ = [("dt_fs", ct.c_double), ("steps_per_sample", ct.c_int), ("n1", ct.c_int),
+                ("n3", ct.c_int), ("n_t2", ct.c_int), ("t2_fs", ct.POINTER(ct.c_double))]
+
+
+class heom_hier_info(ct.Structure):
+    _fields_ = [("d", ct.c_int), ("n_ado", ct.c_int), ("n_exp", ct.c_int), ("n_modes", ct.c_int),
+                ("precision", ct.c_int), ("beta", ct.c_double)]
+
+
+_lib = None
+_P = ct.c_void_p
+_D = ct.POINTER(ct.c_double)
+
+
+def lib():
+    """Load libheom2dvs.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libheom2dvs.so not found at %s; run __graft_entry__.build()" % LIB_PATH)
+    L = ct.CDLL(LIB_PATH)
+    sig = {
+        "heom_build_hierarchy": [ct.POINTER(heom_model), ct.POINTER(_P)],
+        "heom_get_info": [_P, ct.POINTER(heom_hier_info)],
+        "heom_get_operators": [_P, _D, _D, _D, _D, ct.POINTER(ct.c_int32)],
+        "heom_get_mode": [_P, ct.c_int, _D, _D],
+        "heom_equilibrate": [_P, ct.c_double, ct.c_double, ct.c_double, ct.POINTER(_P)],
+        "heom_state_create": [_P, ct.c_int, ct.c_int, ct.POINTER(_P)],
+        "heom_state_upload": [_P, _D],
+        "heom_state_download": [_P, _D],
+        "heom_propagate": [_P, _P, ct.c_double, ct.c_int64],
+        "heom_kick": [_P, _P, ct.c_int],
+        "heom_trace": [_P, _P, ct.c_int, _D],
+        "heom_response_2d": [_P, _P, ct.POINTER(heom_grid), _D, _D, _D],
+        "heom_response_1d": [_P, _P, ct.c_double, ct.c_int, ct.c_int, _D, _D],
+        "heom_propagate_dev": [_P, _P, _P, _P, ct.c_int, ct.c_int, ct.c_double, ct.c_int64, _P],
+        "heom_response_2d_rows": [_P, _P, ct.POINTER(heom_grid), ct.c_int, ct.c_int, _D, _D],
+        "heom_state_broadcast": [_P, _P],
+        "heom_trace_dev": [_P, _P, ct.c_int, ct.c_int, ct.c_int, _P, _P],
+        "heom_kick_dev": [_P, _P, _P, ct.c_int, ct.c_int, ct.c_int, _P],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ct.c_int
+    L.heom_free_hier.argtypes = [_P]
+    L.heom_free_hier.restype = None
+    L.heom_free_state.argtypes = [_P]
+    L.heom_free_state.restype = None
+    L.heom_last_error.restype = ct.c_char_p
+    L.heom_launch_count.restype = ct.c_uint64
+    L.heom_state_device_ptr.argtypes = [_P]
+    L.heom_state_device_ptr.restype = _P
+    L.heom_state_branches.argtypes = [_P]
+    L.heom_state_branches.restype = ct.c_int
+    _lib = L
+    return L
+
+
+def _check(rc, allow=()):
+    if rc != 0 and rc not in allow:
+        raise HeomError(rc, lib().heom_last_error().decode())
+    return rc
+
+
+def _dptr(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+POTENTIAL = {"cubic": 0, "harmonic": 0, "morse": 1}
+
+
+def marshal_model(model, precision=FP64):
+    """heom_model struct from a model dictionary (keeps the arrays alive on the struct)."""
+    modes = (heom_mode * len(model["modes"]))()
+    for i, md in enumerate(model["modes"]):
+        modes[i] = heom_mode(POTENTIAL[md["potential"]], md["omega_cm"], md["g3_cm"],
+                             md["morse_D_cm"], md["n_levels"], md["n_prim"], md["q_min"],
+                             md["q_max"], md["zeta_cm"], md["gamma_cm"], md["V_LL"], md["V_SL"],
+                             md["mu1"], md["mu2"], md["K_pade"])
+    npair = len(model["pairs"])
+    pairs = (heom_pair * max(1, npair))()
+    for i, pr in enumerate(model["pairs"]):
+        pairs[i] = heom_pair(pr["s"], pr["t"], pr["g_st_cm"], pr["g_s2t_cm"], pr["g_st2_cm"],
+                             pr["mu_st"])
+    m = heom_model(len(model["modes"]), modes, npair, pairs, model["T_K"], model["depth_L"],
+                   precision)
+    m._keep = (modes, pairs)
+    return m
+
+
+def marshal_grid(grid):
+    t2 = np.ascontiguousarray(grid["t2_fs"], dtype=np.float64)
+    g = heom_grid(grid["dt_fs"], grid["steps_per_sample"], grid["n1"], grid["n3"], len(t2),
+                  t2.ctypes.data_as(_D))
+    g._keep = t2
+    return g
+
+
+class Hier:
+    """Owning wrapper of a heom_hier handle."""
+
+    def __init__(self, handle):
+        self.h = handle
+        info = heom_hier_info()
+        _check(lib().heom_get_info(self.h, ct.byref(info)))
+        self.d, self.n_ado, self.n_exp = info.d, info.n_ado, info.n_exp
+        self.n_modes, self.precision, self.beta = info.n_modes, info.precision, info.beta
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.heom_free_hier(self.h)
+            self.h = None
+
+
+class State:
+    """Owning wrapper of a heom_state handle."""
+
+    def __init__(self, handle, hier, branches, precision):
+        self.h, self.hier, self.branches, self.precision = handle, hier, branches, precision
+
+    @property
+    def shape(self):
+        return (self.branches, self.hier.n_ado, self.hier.d, self.hier.d)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.heom_free_state(self.h)
+            self.h = None
+
+
+def heom_build_hierarchy(model, precision=FP64):
+    m = marshal_model(model, precision)
+    out = _P()
+    _check(lib().heom_build_hierarchy(ct.byref(m), ct.byref(out)))
+    return Hier(out)
+
+
+def heom_get_operators(h):
+    d, D, N = h.d, h.n_exp, h.n_ado
+    H = np.zeros((d, d))
+    mu = np.zeros((d, d))
+    mup = np.zeros((d, d))
+    bath = np.zeros((D, 4))
+    ado = np.zeros((N, D), dtype=np.int32)
+    _check(lib().heom_get_operators(h.h, _dptr(H), _dptr(mu), _dptr(mup), _dptr(bath),
+                                    ado.ctypes.data_as(ct.POINTER(ct.c_int32))))
+    return {"H": H, "mu": mu, "mu_plus": mup, "bath": bath, "ado": ado}
+
+
+def heom_get_mode(h, s, n):
+    E = np.zeros(n)
+    qk = np.zeros((4, n, n))
+    _check(lib().heom_get_mode(h.h, s, _dptr(E), _dptr(qk)))
+    return E, qk
+
+
+def heom_state_create(h, branches, precision=FP64):
+    out = _P()
+    _check(lib().heom_state_create(h.h, branches, precision, ct.byref(out)))
+    return State(out, h, branches, precision)
+
+
+def heom_state_upload(s, arr):
+    a = np.ascontiguousarray(arr, dtype=np.complex128)
+    if a.shape != s.shape:
+        raise ValueError("state shape %s, array %s" % (s.shape, a.shape))
+    _check(lib().heom_state_upload(s.h, a.ctypes.data_as(_D)))
+
+
+def heom_state_download(s):
+    a = np.zeros(s.shape, dtype=np.complex128)
+    _check(lib().heom_state_download(s.h, a.ctypes.data_as(_D)))
+    return a
+
+
+def heom_equilibrate(h, dt_fs, t_max_fs, tol=0.0):
+    out = _P()
+    rc = _check(lib().heom_equilibrate(h.h, dt_fs, t_max_fs, tol, ct.byref(out)), allow=(-6,))
+    s = State(out, h, 1, FP64)
+    s.converged = rc == 0
+    return s
+
+
+def heom_propagate(h, s, dt_fs, n_steps):
+    _check(lib().heom_propagate(h.h, s.h, dt_fs, int(n_steps)))
+
+
+def heom_kick(h, s, which):
+    _check(lib().heom_kick(h.h, s.h, which))
+
+
+def heom_trace(h, s, order):
+    out = np.zeros(s.branches, dtype=np.complex128)
+    _check(lib().heom_trace(h.h, s.h, order, out.ctypes.data_as(_D)))
+    return out
+
+
+def heom_response_2d(h, rho_eq, grid):
+    g = marshal_grid(grid)
+    shape = (len(grid["t2_fs"]), grid["n1"], grid["n3"])
+    RI = np.zeros(shape, dtype=np.complex128)
+    RII = np.zeros(shape, dtype=np.complex128)
+    SC = np.zeros(shape)
+    _check(lib().heom_response_2d(h.h, rho_eq.h, ct.byref(g), RI.ctypes.data_as(_D),
+                                  RII.ctypes.data_as(_D), SC.ctypes.data_as(_D)))
+    return RI, RII, SC
+
+
+def heom_response_2d_rows(h, rho_eq, grid, j0, j1):
+    g = marshal_grid(grid)
+    shape = (len(grid["t2_fs"]), j1 - j0, grid["n3"])
+    RI = np.zeros(shape, dtype=np.complex128)
+    RII = np.zeros(shape, dtype=np.complex128)
+    _check(lib().heom_response_2d_rows(h.h, rho_eq.h, ct.byref(g), j0, j1, RI.ctypes.data_as(_D),
+                                       RII.ctypes.data_as(_D)))
+    return RI, RII
+
+
+def heom_state_broadcast(src, dst):
+    _check(lib().heom_state_broadcast(src.h, dst.h))
+
+
+def heom_state_device_ptr(s):
+    return int(lib().heom_state_device_ptr(s.h) or 0)
+
+
+def heom_trace_dev(h, state_ptr, branches, precision, order, out_ptr, stream_ptr):
+    _check(lib().heom_trace_dev(h.h, _P(state_ptr), branches, precision, order, _P(out_ptr),
+                                _P(stream_ptr)))
+
+
+def heom_kick_dev(h, in_ptr, out_ptr, branches, precision, which, stream_ptr):
+    _check(lib().heom_kick_dev(h.h, _P(in_ptr), _P(out_ptr), branches, precision, which,
+                               _P(stream_ptr)))
+
+
+def heom_response_1d(h, rho_eq, dt_fs, m, n):
+    R1 = np.zeros(n, dtype=np.complex128)
+    I = np.zeros(n)
+    _check(lib().heom_response_1d(h.h, rho_eq.h, dt_fs, m, n, R1.ctypes.data_as(_D), _dptr(I)))
+    return R1, I
+
+
+def heom_propagate_dev(h, state_ptr, scratch_a_ptr, scratch_b_ptr, branches, precision, dt_fs,
+                       n_steps, stream_ptr):
+    """Device-pointer propagation (pointers as ints, e.g. torch tensor.data_ptr())."""
+    _check(lib().heom_propagate_dev(h.h, _P(state_ptr), _P(scratch_a_ptr), _P(scratch_b_ptr),
+                                    branches, precision, dt_fs, int(n_steps), _P(stream_ptr)))
+
+
+def heom_launch_count():
+    return int(lib().heom_launch_count())
+
+
+def heom_last_error():
+    return lib().heom_last_error().decode()
+
+
+def spectrum_2d(model, grid, precision=FP64):
+    """Whole 2D procedure through the C ABI: build, equilibrate, R_I/R_II, S_C."""
+    h = heom_build_hierarchy(model, precision)
+    eq = heom_equilibrate(h, grid["dt_fs"], grid["t_eq_fs"], 0.0)
+    RI, RII, SC = heom_response_2d(h, eq, grid)
+    return h, eq, RI, RII, SC

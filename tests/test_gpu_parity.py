@@ -1,0 +1,200 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances
+  FP64 path : 1e-10 relative to the max-norm of the compared quantity.
+  FP32 path : states after a few steps within 2e-5 of the max-norm; spectra
+              within 1e-4 of the spectrum max-norm.
+Sizes span several thread blocks with ragged tails (d = 6, 9, 12, 64, 125;
+n1, n3 not multiples of anything), plus the full workload shapes in the batched
+launch configuration, checked on sampled branches.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import heom as OH
+from oracle import model as OM
+
+pytestmark = pytest.mark.gpu
+
+H = pytest.importorskip("paper_2601_20550_gb300.heom")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    import os
+    if not os.path.exists(H.LIB_PATH):
+        import __graft_entry__
+        __graft_entry__.build()
+
+
+def rand_state(shape, seed, hermitian=False):
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+    if hermitian:
+        x = x + np.conj(np.swapaxes(x, -1, -2))
+    return x
+
+
+def rel(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("name,model_fn", [
+    ("two_mode", lambda: W.small_two_mode(n1=3, n2=3, depth_L=3, K_pade=2)),
+    ("three_mode", lambda: W.small_three_mode(n=2, depth_L=2)),
+    ("c1", lambda: W.config("c1")[0]),
+])
+def test_propagate_fp64(name, model_fn):
+    model = model_fn()
+    prob = OM.Problem(model)
+    h = H.heom_build_hierarchy(model)
+    x = rand_state((3, prob.nado, prob.d, prob.d), 11)
+    s = H.heom_state_create(h, 3, H.FP64)
+    H.heom_state_upload(s, x)
+    H.heom_propagate(h, s, 0.5, 6)
+    got = H.heom_state_download(s)
+    ref = OH.propagate(prob, x, 0.5, 6)
+    assert rel(got, ref) < 1e-12
+
+
+def test_propagate_fp32():
+    model = W.small_two_mode(n1=4, n2=3, depth_L=3)
+    prob = OM.Problem(model)
+    h = H.heom_build_hierarchy(model, H.FP32)
+    x = rand_state((2, prob.nado, prob.d, prob.d), 12)
+    s = H.heom_state_create(h, 2, H.FP32)
+    H.heom_state_upload(s, x)
+    H.heom_propagate(h, s, 0.5, 4)
+    got = H.heom_state_download(s)
+    ref = OH.propagate(prob, x, 0.5, 4)
+    assert rel(got, ref) < 2e-5
+
+
+def test_kicks_and_trace():
+    model = W.small_two_mode(n1=3, n2=4, depth_L=2)
+    prob = OM.Problem(model)
+    h = H.heom_build_hierarchy(model)
+    x = rand_state((2, prob.nado, prob.d, prob.d), 13)
+    for which, K in ((0, prob.sys.mu), (1, prob.sys.mu_plus), (2, prob.sys.mu_minus)):
+        s = H.heom_state_create(h, 2, H.FP64)
+        H.heom_state_upload(s, x)
+        H.heom_kick(h, s, which)
+        assert rel(H.heom_state_download(s), OH.kick(x, K)) < 1e-13
+    s = H.heom_state_create(h, 2, H.FP64)
+    H.heom_state_upload(s, x)
+    tr = H.heom_trace(h, s, 3)
+    assert rel(tr, (1j) ** 3 * OH.trace_mu(prob, x)) < 1e-13
+
+
+def test_equilibrate_fixed_time():
+    model = W.small_two_mode(n1=3, n2=3, depth_L=3)
+    prob = OM.Problem(model)
+    h = H.heom_build_hierarchy(model)
+    eq = H.heom_equilibrate(h, 0.5, 50.0, 0.0)
+    got = H.heom_state_download(eq)
+    ref, _, _ = OH.equilibrate(prob, 0.5, t_eq_fs=50.0)
+    assert rel(got, ref) < 1e-11
+
+
+def test_equilibrate_tolerance_mode():
+    model = W.harmonic_bo(omega_cm=300.0, n_levels=6, lambda_cm=60.0, gamma_cm=150.0,
+                          depth_L=2, K_pade=1)
+    prob = OM.Problem(model)
+    h = H.heom_build_hierarchy(model)
+    eq = H.heom_equilibrate(h, 1.0, 20000.0, 1e-10)
+    assert eq.converged
+    ref, _, conv = OH.equilibrate(prob, 1.0, tol=1e-13, t_max_fs=20000.0, check_every=500)
+    assert rel(H.heom_state_download(eq), ref) < 1e-8
+    # an unreachable tolerance reports HEOM_ENOTCONV but still returns the state
+    eq2 = H.heom_equilibrate(h, 1.0, 200.0, 1e-14)
+    assert not eq2.converged
+
+
+@pytest.mark.parametrize("model_fn,grid", [
+    (lambda: W.small_two_mode(n1=3, n2=3, depth_L=2),
+     W.grid(0.5, 4, 7, 5, (0.0, 6.0), t_eq_fs=30.0)),
+    (lambda: W.small_three_mode(n=2, depth_L=2), W.grid(0.5, 3, 5, 6, (2.0,), t_eq_fs=10.0)),
+])
+def test_response_2d_fp64_small(model_fn, grid):
+    model = model_fn()
+    prob = OM.Problem(model)
+    _, _, RI, RII, SC = H.spectrum_2d(model, grid, H.FP64)
+    _, RIo, RIIo, SCo = OH.spectrum_2d(prob, grid)
+    scale = max(np.abs(RIo).max(), np.abs(RIIo).max())
+    assert np.abs(RI - RIo).max() < 1e-10 * scale
+    assert np.abs(RII - RIIo).max() < 1e-10 * scale
+    assert np.abs(SC - SCo).max() < 1e-10 * np.abs(SCo).max()
+
+
+def test_response_2d_c1_full():
+    model, grid = W.config("c1")
+    prob = OM.Problem(model)
+    _, _, RI, RII, SC = H.spectrum_2d(model, grid, H.FP64)
+    _, RIo, RIIo, SCo = OH.spectrum_2d(prob, grid)
+    scale = max(np.abs(RIo).max(), np.abs(RIIo).max())
+    assert np.abs(RI - RIo).max() < 1e-10 * scale
+    assert np.abs(RII - RIIo).max() < 1e-10 * scale
+    assert np.abs(SC - SCo).max() < 1e-10 * np.abs(SCo).max()
+
+
+def test_response_2d_fp32_spectrum():
+    model = W.small_two_mode(n1=3, n2=3, depth_L=2)
+    grid = W.grid(0.5, 4, 16, 16, (0.0,), t_eq_fs=30.0)
+    prob = OM.Problem(model)
+    _, _, RI, RII, SC = H.spectrum_2d(model, grid, H.FP32)
+    _, RIo, RIIo, SCo = OH.spectrum_2d(prob, grid)
+    assert np.abs(SC - SCo).max() < 1e-4 * np.abs(SCo).max()
+
+
+def test_response_1d():
+    model = W.harmonic_bo(omega_cm=1000.0, n_levels=8, lambda_cm=50.0, gamma_cm=200.0,
+                          depth_L=2, K_pade=1)
+    prob = OM.Problem(model)
+    h = H.heom_build_hierarchy(model)
+    eq = H.heom_equilibrate(h, 0.25, 40.0, 0.0)
+    R1, I = H.heom_response_1d(h, eq, 0.25, 8, 32)
+    ref_eq, _, _ = OH.equilibrate(prob, 0.25, t_eq_fs=40.0)
+    R1o = OH.response_1d(prob, ref_eq, 0.25, 8, 32)
+    assert rel(R1, R1o) < 1e-11
+    w = np.ones(32)
+    w[0] = 0.5
+    Io = (2.0 * np.fft.ifft(w * R1o) * 32).imag
+    assert rel(I, Io) < 1e-11
+
+
+@pytest.mark.parametrize("name,precision,tol,branches", [
+    ("c2", 0, 1e-11, 256),
+    ("c3", 1, 2e-5, 256),
+])
+def test_full_size_batched_step_sampled(name, precision, tol, branches):
+    """Full workload shape in the bench's batched launch (all branches at once),
+    through the device-pointer entry point on a torch stream; one RK4 step,
+    sampled branches against the oracle."""
+    torch = pytest.importorskip("torch")
+    model, grid = W.config(name)
+    h = H.heom_build_hierarchy(model, precision)
+    nado, d = h.n_ado, h.d
+    cdt = torch.complex128 if precision == 0 else torch.complex64
+    dev = torch.device("cuda:0")
+    y = torch.zeros((branches, nado, d, d), dtype=cdt, device=dev)
+    wa = torch.empty_like(y)
+    wb = torch.empty_like(y)
+    rng = np.random.default_rng(21)
+    samples = [0, branches - 1]
+    xs = {}
+    for b in samples:
+        xs[b] = rng.standard_normal((nado, d, d)) + 1j * rng.standard_normal((nado, d, d))
+        y[b].copy_(torch.from_numpy(xs[b]).to(cdt))
+    stream = torch.cuda.current_stream()
+    H.heom_propagate_dev(h, y.data_ptr(), wa.data_ptr(), wb.data_ptr(), branches, precision,
+                         grid["dt_fs"], 1, stream.cuda_stream)
+    torch.cuda.synchronize()
+    prob = OM.Problem(model)
+    for b in samples:
+        got = y[b].cpu().numpy().astype(np.complex128)
+        ref = OH.rk4_step(prob, xs[b][None].astype(np.complex64 if precision else np.complex128)
+                          .astype(np.complex128), grid["dt_fs"])[0]
+        assert rel(got, ref) < tol
+    # a branch that started at zero stays zero
+    assert float(y[branches // 2].abs().max()) == 0.0
