@@ -39,7 +39,7 @@ WORKLOADS = {
     "c3-fp64": ("c3", 0, 2),
     "c1-fp64": ("c1", 0, 64),
 }
-PREC_NAME = {0: "f64", 1: "f32", 2: "bf16x3-f32"}
+PREC_NAME = {0: "f64", 1: "f32", 2: "fp16x2-tc-f32acc"}
 
 
 def describe(cfg, model, grid, d, nado):
@@ -210,8 +210,11 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="c2-fp64", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--e2e-rows", type=int, default=0, help="t1 rows per e2e step (default per workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--branches", type=int, default=0,
+                    help="override the batch (profiling runs only; default 2*n1)")
     args = ap.parse_args()
     cfg, prec, e2e_rows = WORKLOADS[args.workload]
 
@@ -235,7 +238,7 @@ def main():
     d, nado = h.d, h.n_ado
     eq = H.heom_equilibrate(h, grid["dt_fs"], grid["t_eq_fs"], 0.0)
     m = grid["steps_per_sample"]
-    B = 2 * grid["n1"]
+    B = args.branches if args.branches > 0 else 2 * grid["n1"]
     cdt = torch.complex128 if prec == 0 else torch.complex64
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
@@ -331,7 +334,7 @@ def main():
         eq_host = H.heom_state_download(eq)
         pinned = torch.from_numpy(eq_host.view(np.float64)).pin_memory()
         eq_up = H.heom_state_create(h, 1, 0)
-        rows = min(e2e_rows, grid["n1"])
+        rows = min(args.e2e_rows or e2e_rows, grid["n1"])
         # warm-up call on one row
         H.heom_response_2d_rows(h, eq, grid, 0, 1)
         tt = []
@@ -341,7 +344,7 @@ def main():
             j1 = min(grid["n1"], j0 + rows)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            H.lib().heom_state_upload(eq_up.h, H._P(pinned.data_ptr()))
+            H.lib().heom_state_upload(eq_up.h, H.ct.cast(pinned.data_ptr(), H._D))
             RI, RII = H.heom_response_2d_rows(h, eq_up, grid, j0, j1)
             tt.append((time.perf_counter() - t0, rows_ado_updates(grid, nado, j0, j1)))
             d2h = RI.nbytes + RII.nbytes
@@ -358,6 +361,7 @@ def main():
 
     if rank == 0:
         conf = describe(cfg, model, grid, d, nado)
+        conf["branches"] = B
         conf.update({"parallelism": "replicas" if world > 1 else "single-gpu",
                      "l2": "inputs larger than L2 (state %.1f GB)" % (y.numel() * y.element_size() / 1e9),
                      "precision": PREC_NAME[prec]})

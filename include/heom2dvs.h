@@ -47,8 +47,9 @@ typedef enum {
 /* Arithmetic of the propagation.  The equilibrium hierarchy is always FP64. */
 typedef enum {
   HEOM_FP64 = 0,        /* complex128 state, FP64 right-hand side */
-  HEOM_FP32 = 1,        /* complex64 state, FP32 right-hand side (CUDA cores) */
-  HEOM_BF16X3 = 2       /* complex64 state, split-BF16 tensor-core products, FP32 accumulation */
+  HEOM_FP32 = 1,        /* complex64 state, FP32 right-hand side on CUDA cores */
+  HEOM_TC = 2           /* complex64 state; [H', rho] on tcgen05 tensor cores with split-FP16
+                           operands (per-ADO power-of-two scaling), FP32 accumulation */
 } heom_precision;
 
 /*
@@ -146,7 +147,10 @@ heom_status heom_equilibrate(heom_hier *h, double dt_fs, double t_max_fs, double
                              heom_state **rho_eq);
 
 /* States: create (zeroed), upload/download host arrays [branches][n_ado][d][d]
- * complex (interleaved doubles; FP32 states are converted). */
+ * complex (interleaved doubles) in the product eigenbasis.  Complex64 states
+ * (HEOM_FP32, HEOM_TC) are stored on the device in the coupling eigenbasis,
+ * where every V_s is diagonal (rho' = U^T rho U with U the Kronecker product of
+ * the per-mode eigenvector matrices of V_s); upload and download convert. */
 heom_status heom_state_create(const heom_hier *h, int branches, int precision, heom_state **out);
 heom_status heom_state_upload(heom_state *s, const double *host);
 heom_status heom_state_download(const heom_state *s, double *host);
@@ -203,6 +207,11 @@ heom_status heom_state_broadcast(const heom_state *src, heom_state *dst);
  * complex64); valid until heom_free_state. */
 void *heom_state_device_ptr(heom_state *s);
 
+/* Device-to-device copy of a state's storage to / from a caller buffer of the
+ * same size and representation, on a caller stream (no synchronisation). */
+heom_status heom_state_export_dev(const heom_state *s, void *dst, void *stream);
+heom_status heom_state_import_dev(heom_state *s, const void *src, void *stream);
+
 /*
  * Linear response R1(t) = i tr{mu G(t) mu^x rho_eq} at t = k m dt, k < n (Eq. R1),
  * into R1 [n] complex, and the absorption I(Omega_p) = Im[dtau sum_k w_k
@@ -214,8 +223,9 @@ heom_status heom_response_1d(heom_hier *h, const heom_state *rho_eq, double dt_f
 /*
  * Device-pointer RK4 propagation on a caller stream: state and two scratch
  * buffers of the same size, each [branches][n_ado][d][d] complex (complex128 for
- * HEOM_FP64, complex64 otherwise), row-major, ADO stride d*d.  No allocation,
- * no synchronisation; the result is in state.
+ * HEOM_FP64 in the product eigenbasis; complex64 in the coupling eigenbasis
+ * otherwise), row-major, ADO stride d*d.  No allocation, no synchronisation;
+ * the result is in state.  HEOM_TC requires a hierarchy built with HEOM_TC.
  */
 heom_status heom_propagate_dev(heom_hier *h, void *state, void *scratch_a, void *scratch_b,
                                int branches, int precision, double dt_fs, int64_t n_steps,

@@ -102,9 +102,14 @@ struct heom_hier {
   double *mu64 = nullptr, *mup64 = nullptr, *mum64 = nullptr;
   float *mu32 = nullptr, *mup32 = nullptr, *mum32 = nullptr;
   double *mu_trace = nullptr;   // FP64 mu for traces
-  TcOperators tc{};             // tensor-core operator tiles (HEOM_BF16X3)
+  TcOperators tc{};             // tensor-core operator tiles (HEOM_TC)
+  VbModel vb{};                 // coupling-eigenbasis model (FP32 paths)
+  double *U64 = nullptr, *UT64 = nullptr;        // coupling eigenbasis U and U^T
+  float *mu_vb32 = nullptr, *mup_vb32 = nullptr, *mum_vb32 = nullptr;
+  double *mu_vb64 = nullptr;                     // mu in the coupling basis (traces)
   bool on_device = false;
   ~heom_hier() {
+    if (tc.maxbuf) cudaFree(tc.maxbuf);
     for (void *p : allocs) cudaFree(p);
     if (stream) cudaStreamDestroy(stream);
   }
@@ -118,6 +123,7 @@ struct heom_hier {
 
 struct heom_state {
   int branches = 0, precision = 0, d = 0, n_ado = 0;
+  heom_hier *hier = nullptr;     // owner of the basis transforms (not owned)
   DeviceBuffer buf;
   int64_t elems() const { return (int64_t)branches * n_ado * d * d; }
   size_t elem_bytes() const { return precision == HEOM_FP64 ? 16 : 8; }
@@ -157,7 +163,9 @@ static const R *mu_of(heom_hier *h, int which);
 template <>
 const double *mu_of<double>(heom_hier *h, int which) { return which == 0 ? h->mu64 : which == 1 ? h->mup64 : h->mum64; }
 template <>
-const float *mu_of<float>(heom_hier *h, int which) { return which == 0 ? h->mu32 : which == 1 ? h->mup32 : h->mum32; }
+const float *mu_of<float>(heom_hier *h, int which) {
+  return which == 0 ? h->mu_vb32 : which == 1 ? h->mup_vb32 : h->mum_vb32;
+}
 
 // Necessary condition for RK4 stability: the largest Bohr frequency of H_S' and
 // the largest ADO decay rate must each lie inside the RK4 region (|z| < 2.78 on
@@ -185,8 +193,22 @@ static void rk4_steps(heom_hier *h, typename CxT<R>::type *y, typename CxT<R>::t
   const DevModel<R> &dm = dev_model<R>(h);
   const int64_t total = (int64_t)branches * dm.n_ado * dm.d * dm.d;
   if (total == 0 || nsteps <= 0) return;
-  if (precision == HEOM_BF16X3 && tc_supported(h->tc)) {
-    tc_rk4_steps(h->tc, (float2 *)y, (float2 *)wa, (float2 *)wb, branches, dt, nsteps, st);
+  if (sizeof(R) == 4) {
+    float2 *fy = (float2 *)y, *fa = (float2 *)wa, *fb = (float2 *)wb;
+    if (precision == HEOM_TC) {
+      if (!tc_supported(h->tc)) throw Fail{HEOM_EINVAL, "tensor-core path not prepared for this hierarchy"};
+      tc_rk4_steps(h->tc, fy, fa, fb, branches, dt, nsteps, st);
+    } else {
+      const int grid = grid_for(total);
+      for (int64_t s = 0; s < nsteps; ++s) {
+        stage_kernel_vb<<<grid, 256, 0, st>>>(fy, fy, fa, (float)(dt / 4), h->vb, total);
+        stage_kernel_vb<<<grid, 256, 0, st>>>(fa, fy, fb, (float)(dt / 3), h->vb, total);
+        stage_kernel_vb<<<grid, 256, 0, st>>>(fb, fy, fa, (float)(dt / 2), h->vb, total);
+        stage_kernel_vb<<<grid, 256, 0, st>>>(fa, fy, fy, (float)dt, h->vb, total);
+        count_launch(4);
+      }
+    }
+    LAUNCH_CHECK();
     return;
   }
   const int grid = grid_for(total);
@@ -214,7 +236,8 @@ template <typename R>
 static void trace_into(heom_hier *h, const typename CxT<R>::type *w, int branches, int order,
                        double2 *out, int64_t ostride, cudaStream_t st) {
   const Model &M = h->M;
-  trace_kernel<R><<<branches, 256, 0, st>>>(w, h->mu_trace, M.d, M.n_ado, order, out, ostride);
+  const double *mu = sizeof(R) == 8 ? h->mu_trace : h->mu_vb64;
+  trace_kernel<R><<<branches, 256, 0, st>>>(w, mu, M.d, M.n_ado, order, out, ostride);
   count_launch(1);
   LAUNCH_CHECK();
 }
@@ -222,6 +245,35 @@ static void trace_into(heom_hier *h, const typename CxT<R>::type *w, int branche
 // ---------------------------------------------------------------------------
 // 2D response (Sec. II.C.2) in precision R.
 // ---------------------------------------------------------------------------
+// Original-basis complex128 ADOs -> coupling-basis complex64 (U^T x U), and back.
+static void to_coupling_basis(heom_hier *h, const double2 *x, float2 *out, int64_t elems, cudaStream_t st) {
+  DeviceBuffer tmp(elems * 16);
+  sim_left_kernel<double2><<<grid_for(elems), 256, 0, st>>>(x, (double2 *)tmp.p, h->U64, h->M.d, elems);
+  sim_right_kernel<float2><<<grid_for(elems), 256, 0, st>>>((const double2 *)tmp.p, out, h->U64, h->M.d, elems);
+  count_launch(2);
+  LAUNCH_CHECK();
+  CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+static void from_coupling_basis(heom_hier *h, const float2 *x, double2 *out, int64_t elems, cudaStream_t st) {
+  DeviceBuffer tmp(elems * 16);
+  sim_left_kernel<float2><<<grid_for(elems), 256, 0, st>>>(x, (double2 *)tmp.p, h->UT64, h->M.d, elems);
+  sim_right_kernel<double2><<<grid_for(elems), 256, 0, st>>>((const double2 *)tmp.p, out, h->UT64, h->M.d, elems);
+  count_launch(2);
+  LAUNCH_CHECK();
+  CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+static void check_tc_error(heom_hier *h) {
+  if (!h->tc.ready) return;
+  int e = 0;
+  CUDA_TRY(cudaMemcpy(&e, h->tc.err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    CUDA_TRY(cudaMemset(h->tc.err, 0, sizeof(int)));
+    throw Fail{HEOM_ETIMEOUT, "a tensor-core stage wait ran out"};
+  }
+}
+
 // Rows [jr0, jr1) of R_I and R_II into Rdev laid out [n_t2][2][jr1 - jr0][n3].
 template <typename R>
 static void response_2d_rows_impl(heom_hier *h, const heom_state *eq, const heom_grid *g, int jr0, int jr1,
@@ -248,9 +300,7 @@ static void response_2d_rows_impl(heom_hier *h, const heom_state *eq, const heom
   if (sizeof(R) == 8) {
     CUDA_TRY(cudaMemcpyAsync(eqR.p, eq->buf.p, per_branch * cb, cudaMemcpyDeviceToDevice, st));
   } else {
-    convert_f64_to_f32<<<grid_for(per_branch), 256, 0, st>>>((const double2 *)eq->buf.p, (float2 *)eqR.p, per_branch);
-    count_launch(1);
-    LAUNCH_CHECK();
+    to_coupling_basis(h, (const double2 *)eq->buf.p, (float2 *)eqR.p, per_branch, st);
   }
   // branch chunk size: both pathways of jc t1 samples, 3 or 4 state sets
   const int nsets = nt2 > 1 ? 4 : 3;
@@ -343,7 +393,35 @@ static void ensure_device(heom_hier *h) {
   h->mup32 = h->up(cast_vec<float>(M.mu_plus));
   h->mum32 = h->up(cast_vec<float>(mum));
   h->mu_trace = h->mu64;
-  if (M.precision == HEOM_BF16X3) tc_build(h->tc, M, h->dm32, h->allocs);
+  // coupling eigenbasis (FP32 and tensor-core paths)
+  std::vector<double> UT((size_t)M.d * M.d), mumv((size_t)M.d * M.d);
+  for (int a = 0; a < M.d; ++a)
+    for (int b = 0; b < M.d; ++b) {
+      UT[(size_t)a * M.d + b] = M.vb_U[(size_t)b * M.d + a];
+      mumv[(size_t)a * M.d + b] = M.vb_mu_plus[(size_t)b * M.d + a];
+    }
+  h->U64 = h->up(M.vb_U);
+  h->UT64 = h->up(UT);
+  h->mu_vb64 = h->up(M.vb_mu);
+  h->mu_vb32 = h->up(cast_vec<float>(M.vb_mu));
+  h->mup_vb32 = h->up(cast_vec<float>(M.vb_mu_plus));
+  h->mum_vb32 = h->up(cast_vec<float>(mumv));
+  std::vector<float> lam((size_t)M.n_modes * M.d);
+  for (int s = 0; s < M.n_modes; ++s)
+    for (int a = 0; a < M.d; ++a) lam[(size_t)s * M.d + a] = (float)M.vb_lam[s][(a / M.stride[s]) % M.dims[s]];
+  VbModel vb{};
+  vb.d = M.d;
+  vb.n_ado = M.n_ado;
+  vb.n_modes = M.n_modes;
+  vb.H = h->up(cast_vec<float>(M.vb_H));
+  vb.lam = h->up(lam);
+  vb.decay = d64.decay;
+  vb.nb_off = d64.nb_off;
+  vb.nb_idx = d64.nb_idx;
+  vb.nb_cA = d32.nb_cA;
+  vb.nb_cB = d32.nb_cB;
+  h->vb = vb;
+  if (M.precision == HEOM_TC) tc_build(h->tc, M, h->vb, h->allocs);
   h->on_device = true;
 }
 
@@ -423,6 +501,7 @@ heom_status heom_state_create(const heom_hier *h, int branches, int precision, h
     s->precision = precision;
     s->d = h->M.d;
     s->n_ado = h->M.n_ado;
+    s->hier = const_cast<heom_hier *>(h);
     try {
       s->buf.alloc(s->elems() * s->elem_bytes());
       CUDA_TRY(cudaMemset(s->buf.p, 0, s->buf.bytes));
@@ -446,10 +525,7 @@ heom_status heom_state_upload(heom_state *s, const double *host) {
     } else {
       DeviceBuffer tmp(n * 16);
       CUDA_TRY(cudaMemcpy(tmp.p, host, n * 16, cudaMemcpyHostToDevice));
-      convert_f64_to_f32<<<grid_for(n), 256>>>((const double2 *)tmp.p, (float2 *)s->buf.p, n);
-      count_launch(1);
-      LAUNCH_CHECK();
-      CUDA_TRY(cudaDeviceSynchronize());
+      to_coupling_basis(s->hier, (const double2 *)tmp.p, (float2 *)s->buf.p, n, s->hier->stream);
     }
     return HEOM_OK;
   });
@@ -463,9 +539,7 @@ heom_status heom_state_download(const heom_state *s, double *host) {
       CUDA_TRY(cudaMemcpy(host, s->buf.p, n * 16, cudaMemcpyDeviceToHost));
     } else {
       DeviceBuffer tmp(n * 16);
-      convert_f32_to_f64<<<grid_for(n), 256>>>((const float2 *)s->buf.p, (double2 *)tmp.p, n);
-      count_launch(1);
-      LAUNCH_CHECK();
+      from_coupling_basis(s->hier, (const float2 *)s->buf.p, (double2 *)tmp.p, n, s->hier->stream);
       CUDA_TRY(cudaMemcpy(host, tmp.p, n * 16, cudaMemcpyDeviceToHost));
     }
     return HEOM_OK;
@@ -485,6 +559,7 @@ heom_status heom_propagate(heom_hier *h, heom_state *rho, double dt_fs, int64_t 
     else
       rk4_steps<float>(h, (float2 *)rho->buf.p, (float2 *)a.p, (float2 *)b.p, rho->branches, dt_fs, n_steps, h->stream, rho->precision);
     CUDA_TRY(cudaStreamSynchronize(h->stream));
+    check_tc_error(h);
     return HEOM_OK;
   });
 }
@@ -626,6 +701,8 @@ heom_status heom_response_2d(heom_hier *h, const heom_state *rho_eq, const heom_
     DeviceBuffer Rdev((size_t)nt2 * 2 * n1 * n3 * 16), SCdev((size_t)nt2 * n1 * n3 * 8);
     CUDA_TRY(cudaMemsetAsync(Rdev.p, 0, Rdev.bytes, h->stream));
     rows_dispatch(h, rho_eq, g, 0, n1, (double2 *)Rdev.p);
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    check_tc_error(h);
     const double dtau = g->dt_fs * g->steps_per_sample;
     for (int it = 0; it < nt2; ++it) {
       double2 *RI = (double2 *)Rdev.p + (int64_t)it * 2 * n1 * n3;
@@ -661,6 +738,8 @@ heom_status heom_response_2d_rows(heom_hier *h, const heom_state *rho_eq, const 
     DeviceBuffer Rdev((size_t)nt2 * 2 * nr * n3 * 16);
     CUDA_TRY(cudaMemsetAsync(Rdev.p, 0, Rdev.bytes, h->stream));
     rows_dispatch(h, rho_eq, g, j0, j1, (double2 *)Rdev.p);
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    check_tc_error(h);
     std::vector<double> Rh((size_t)nt2 * 2 * nr * n3 * 2);
     CUDA_TRY(cudaMemcpyAsync(Rh.data(), Rdev.p, Rdev.bytes, cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
@@ -679,26 +758,40 @@ heom_status heom_state_broadcast(const heom_state *src, heom_state *dst) {
   if (!src || !dst || src->d != dst->d || src->n_ado != dst->n_ado) return fail(HEOM_EINVAL, "bad broadcast arguments");
   return guarded([&]() -> heom_status {
     const int64_t per = (int64_t)src->n_ado * src->d * src->d;
-    for (int b = 0; b < dst->branches; ++b) {
-      char *out = (char *)dst->buf.p + (size_t)b * per * dst->elem_bytes();
-      if (src->precision == dst->precision) {
-        CUDA_TRY(cudaMemcpy(out, src->buf.p, per * src->elem_bytes(), cudaMemcpyDeviceToDevice));
-      } else if (src->precision == HEOM_FP64) {
-        convert_f64_to_f32<<<grid_for(per), 256>>>((const double2 *)src->buf.p, (float2 *)out, per);
-        count_launch(1);
-        LAUNCH_CHECK();
-      } else {
-        convert_f32_to_f64<<<grid_for(per), 256>>>((const float2 *)src->buf.p, (double2 *)out, per);
-        count_launch(1);
-        LAUNCH_CHECK();
-      }
+    // branch 0 (with the basis/precision conversion), then device copies
+    char *out0 = (char *)dst->buf.p;
+    if (src->precision == dst->precision || (src->precision != HEOM_FP64 && dst->precision != HEOM_FP64)) {
+      CUDA_TRY(cudaMemcpy(out0, src->buf.p, per * src->elem_bytes(), cudaMemcpyDeviceToDevice));
+    } else if (src->precision == HEOM_FP64) {
+      to_coupling_basis(dst->hier, (const double2 *)src->buf.p, (float2 *)out0, per, dst->hier->stream);
+    } else {
+      from_coupling_basis(dst->hier, (const float2 *)src->buf.p, (double2 *)out0, per, dst->hier->stream);
     }
+    for (int b = 1; b < dst->branches; ++b)
+      CUDA_TRY(cudaMemcpy(out0 + (size_t)b * per * dst->elem_bytes(), out0, per * dst->elem_bytes(),
+                          cudaMemcpyDeviceToDevice));
     CUDA_TRY(cudaDeviceSynchronize());
     return HEOM_OK;
   });
 }
 
 void *heom_state_device_ptr(heom_state *s) { return s ? s->buf.p : nullptr; }
+
+heom_status heom_state_export_dev(const heom_state *s, void *dst, void *stream) {
+  if (!s || !dst) return fail(HEOM_EINVAL, "null argument");
+  return guarded([&]() -> heom_status {
+    CUDA_TRY(cudaMemcpyAsync(dst, s->buf.p, s->elems() * s->elem_bytes(), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return HEOM_OK;
+  });
+}
+
+heom_status heom_state_import_dev(heom_state *s, const void *src, void *stream) {
+  if (!s || !src) return fail(HEOM_EINVAL, "null argument");
+  return guarded([&]() -> heom_status {
+    CUDA_TRY(cudaMemcpyAsync(s->buf.p, src, s->elems() * s->elem_bytes(), cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    return HEOM_OK;
+  });
+}
 
 heom_status heom_kick_dev(heom_hier *h, const void *in, void *out, int branches, int precision, int which,
                           void *stream) {

@@ -44,6 +44,48 @@ __global__ void dft1d_kernel(const double2 *__restrict__ R, int n, double dtau, 
   I[p] = dtau * s;
 }
 
+__global__ void __launch_bounds__(256) stage_kernel_vb(const float2 *__restrict__ w, const float2 *y, float2 *out,
+                                                       float alpha, VbModel M, int64_t total) {
+  const int d = M.d;
+  const int64_t dd = (int64_t)d * d;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t el = e % dd;
+    const int64_t bn = e / dd;
+    const int n = (int)(bn % M.n_ado);
+    const int64_t br = bn / M.n_ado;
+    const int a = (int)(el / d), b = (int)(el % d);
+    const float2 *wb = w + br * M.n_ado * dd;
+    const float2 *wn = wb + (int64_t)n * dd;
+    float re = 0.f, im = 0.f;
+    const float *Ha = M.H + (int64_t)a * d;
+    for (int c = 0; c < d; ++c) {
+      const float h1 = Ha[c], h2 = M.H[(int64_t)c * d + b];
+      const float2 x = wn[(int64_t)c * d + b], z = wn[(int64_t)a * d + c];
+      re += h1 * x.x - z.x * h2;
+      im += h1 * x.y - z.y * h2;
+    }
+    float ore = im, oim = -re;
+    const float dec = (float)M.decay[n];
+    const float2 self = wn[el];
+    ore -= dec * self.x;
+    oim -= dec * self.y;
+    for (int s = 0; s < M.n_modes; ++s) {
+      const int o0 = M.nb_off[n * M.n_modes + s], o1 = M.nb_off[n * M.n_modes + s + 1];
+      if (o0 == o1) continue;
+      const float la = M.lam[s * d + a], lb = M.lam[s * d + b];
+      const float f = la - lb, g = la + lb;
+      for (int q = o0; q < o1; ++q) {
+        const float2 x = wb[(int64_t)M.nb_idx[q] * dd + el];
+        const float p = M.nb_cB[q] * g, qq = M.nb_cA[q] * f;
+        ore += p * x.x + qq * x.y;
+        oim += p * x.y - qq * x.x;
+      }
+    }
+    const float2 yv = y[e];
+    out[e] = make_float2(yv.x + alpha * ore, yv.y + alpha * oim);
+  }
+}
+
 __global__ void convert_f64_to_f32(const double2 *__restrict__ x, float2 *__restrict__ y, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = make_float2((float)x[i].x, (float)x[i].y);

@@ -227,6 +227,67 @@ __global__ void dft1d_kernel(const double2 *__restrict__ R, int n, double dtau, 
 __global__ void convert_f64_to_f32(const double2 *__restrict__ x, float2 *__restrict__ y, int64_t n);
 __global__ void convert_f32_to_f64(const float2 *__restrict__ x, double2 *__restrict__ y, int64_t n);
 
+// ---------------------------------------------------------------------------
+// Coupling-eigenbasis representation (mixed-precision paths).  Every V_s is
+// diagonal there, so V_s^x and V_s^o act elementwise with the factors
+// lam_s[a_s] -+ lam_s[b_s]; H' = U^T H_S' U is dense.
+// ---------------------------------------------------------------------------
+struct VbModel {
+  int d, n_ado, n_modes;
+  const float *H;          // d x d, coupling basis
+  const float *lam;        // [n_modes][d]: lam_s[digit_s(a)] for every product index a
+  const double *decay;     // [n_ado]
+  const int *nb_off, *nb_idx;
+  const float *nb_cA, *nb_cB;
+};
+
+// Fused RK4 stage in the coupling basis on CUDA cores (FP32):
+//   out = y + alpha * ( -i [H', w_n] - gamma_n w_n + sum_nb kappa_nb(a, b) w_nb )
+// kappa = -i cA (lam_a - lam_b) + cB (lam_a + lam_b) for the coupling list of (n, s).
+__global__ void __launch_bounds__(256) stage_kernel_vb(const float2 *__restrict__ w, const float2 *y, float2 *out,
+                                                       float alpha, VbModel M, int64_t total);
+
+// Similarity transform of every ADO: out_n = P^T x_n P (double accumulation).
+// Two passes through tmp (double2, same element count as x).
+template <typename Tin>
+__global__ void __launch_bounds__(256) sim_left_kernel(const Tin *__restrict__ x, double2 *__restrict__ tmp,
+                                                       const double *__restrict__ P, int d, int64_t total) {
+  const int64_t dd = (int64_t)d * d;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t el = e % dd;
+    const Tin *xn = x + (e - el);
+    const int a = (int)(el / d), b = (int)(el % d);
+    double re = 0, im = 0;
+    for (int c = 0; c < d; ++c) {
+      const double p = P[(int64_t)c * d + a];
+      re += p * (double)xn[(int64_t)c * d + b].x;
+      im += p * (double)xn[(int64_t)c * d + b].y;
+    }
+    tmp[e] = make_double2(re, im);
+  }
+}
+
+template <typename Tout>
+__global__ void __launch_bounds__(256) sim_right_kernel(const double2 *__restrict__ tmp, Tout *__restrict__ out,
+                                                        const double *__restrict__ P, int d, int64_t total) {
+  const int64_t dd = (int64_t)d * d;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t el = e % dd;
+    const double2 *tn = tmp + (e - el);
+    const int a = (int)(el / d), b = (int)(el % d);
+    double re = 0, im = 0;
+    for (int c = 0; c < d; ++c) {
+      const double p = P[(int64_t)c * d + b];
+      re += tn[(int64_t)a * d + c].x * p;
+      im += tn[(int64_t)a * d + c].y * p;
+    }
+    Tout o;
+    o.x = re;
+    o.y = im;
+    out[e] = o;
+  }
+}
+
 // Per-ADO squared Frobenius norms of one branch: out[n] = ||w_n||_F^2
 template <typename R>
 __global__ void ado_norms_kernel(const typename CxT<R>::type *__restrict__ w, int64_t dd, int n_ado,

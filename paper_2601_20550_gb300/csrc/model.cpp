@@ -370,7 +370,58 @@ Model build_model(const heom_model &m) {
   }
   M.n_exp = (int)M.exp_nu.size();
   build_hierarchy(M);
+  build_coupling_basis(M);
   return M;
+}
+
+// ---------------------------------------------------------------------------
+// Coupling eigenbasis.  Each V_s acts on mode s only, so the product of the
+// per-mode eigenbases of v_s diagonalises every V_s at once.  In that basis
+// V_s^x X and V_s^o X are elementwise: (lam_s[a_s] -+ lam_s[b_s]) X_ab.  The
+// transformation is orthogonal; H_S' and mu become dense d x d matrices.
+// ---------------------------------------------------------------------------
+static std::vector<double> similarity(const std::vector<double> &U, const std::vector<double> &X, int d) {
+  // U^T X U
+  std::vector<double> T((size_t)d * d, 0.0), out((size_t)d * d, 0.0);
+  for (int c = 0; c < d; ++c)
+    for (int a = 0; a < d; ++a) {
+      double u = U[(size_t)c * d + a];
+      if (u == 0.0) continue;
+      for (int b = 0; b < d; ++b) T[(size_t)a * d + b] += u * X[(size_t)c * d + b];
+    }
+  for (int a = 0; a < d; ++a)
+    for (int c = 0; c < d; ++c) {
+      double t = T[(size_t)a * d + c];
+      if (t == 0.0) continue;
+      for (int b = 0; b < d; ++b) out[(size_t)a * d + b] += t * U[(size_t)c * d + b];
+    }
+  return out;
+}
+
+void build_coupling_basis(Model &M) {
+  const int d = M.d;
+  std::vector<std::vector<double>> Us;
+  M.vb_lam.clear();
+  for (int s = 0; s < M.n_modes; ++s) {
+    const int n = M.dims[s];
+    std::vector<double> A = M.Vloc[s], w, Z;
+    jacobi_eigh(A, n, w, Z);
+    M.vb_lam.push_back(w);
+    Us.push_back(Z);
+  }
+  M.vb_U.assign((size_t)d * d, 0.0);
+  for (int a = 0; a < d; ++a)
+    for (int b = 0; b < d; ++b) {
+      double v = 1.0;
+      for (int s = 0; s < M.n_modes && v != 0.0; ++s) {
+        int as = (a / M.stride[s]) % M.dims[s], bs = (b / M.stride[s]) % M.dims[s];
+        v *= Us[s][(size_t)as * M.dims[s] + bs];
+      }
+      M.vb_U[(size_t)a * d + b] = v;
+    }
+  M.vb_H = similarity(M.vb_U, M.H, d);
+  M.vb_mu = similarity(M.vb_U, M.mu, d);
+  M.vb_mu_plus = similarity(M.vb_U, M.mu_plus, d);
 }
 
 // ---------------------------------------------------------------------------

@@ -33,7 +33,14 @@ struct Model {
   std::vector<double> decay;                   // sum_j n_j nu_j
   std::vector<int32_t> nb_off, nb_idx;         // per (ado, mode) coupling lists
   std::vector<double> nb_cA, nb_cB;
+  // coupling eigenbasis: v_s = U_s diag(lam_s) U_s^T per mode; U = U_0 x U_1 x ...
+  std::vector<std::vector<double>> vb_lam;     // per mode, n_s eigenvalues
+  std::vector<double> vb_U;                    // d x d
+  std::vector<double> vb_H, vb_mu, vb_mu_plus; // U^T X U
 };
+
+// Coupling-eigenbasis quantities (fills vb_* of M).
+void build_coupling_basis(Model &M);
 
 void jacobi_eigh(std::vector<double> &A, int n, std::vector<double> &w, std::vector<double> &Z);
 void pade_bose(int N, std::vector<double> &xi, std::vector<double> &eta);

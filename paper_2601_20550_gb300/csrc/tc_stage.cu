@@ -1,22 +1,561 @@
-// Tensor-core (tcgen05) RK4 stage for the mixed-precision path.
+// Tensor-core (tcgen05) RK4 stage of the HEOM right-hand side (Eq. HEOM_DB) for
+// the mixed-precision path, sm_103a.
+//
+// One persistent CTA per SM walks the work items (branch, ADO).  For each item:
+//   1. all 256 threads load w_n (complex64, d x d) from HBM, find its largest
+//      component, scale it by a power of two into FP16 range and split every
+//      component into hi + lo FP16 parts, written to shared memory in the
+//      128-byte-swizzled UMMA layout (re rows 0..127, im rows 128..255);
+//   2. one thread issues tcgen05.mma: D = Z^T H' - H' Z^T = [H', Z]^T with the
+//      H' pieces (hi, mid, lo) resident in shared memory, FP32 accumulation in
+//      tensor memory (256 columns: Re D | Im D);
+//   3. the epilogue reads D from tensor memory (lane = column b of w_n, column =
+//      row a) and updates out += alpha * (-i C - gamma_n w_n) with coalesced
+//      accesses.  The elementwise system-bath terms are written into out before
+//      by vterm_kernel (out = y + alpha * sum kappa w_nb), a streaming kernel that
+//      runs at full occupancy so that enough neighbour loads are in flight.
+// All waits are bounded: on expiry the kernel sets the error word, frees its
+// tensor memory and returns.
 #include "tc_stage.h"
 
+#include <algorithm>
+#include <cmath>
+#include <cstring>
 #include <stdexcept>
+
+#include <cuda_fp16.h>
 
 namespace heom {
 
-void tc_build(TcOperators &tc, const Model &M, const DevModel<float> &dm, std::vector<void *> &allocs) {
-  (void)allocs;
-  tc.d = M.d;
-  tc.dm = dm;
-  tc.ready = false;
-  throw std::invalid_argument("HEOM_BF16X3 is not available for this basis size yet");
+void count_launch(uint64_t n);
+
+namespace {
+
+constexpr int kThreads = 512;
+constexpr int kTcMaxModes = 4;
+constexpr uint32_t kHTile = 32768;               // 128 x 128 FP16
+constexpr uint32_t kZZ = 65536;                  // 256 x 128 FP16 (re | im rows)
+constexpr uint32_t kTiles = 2 * kZZ + 3 * kHTile;
+constexpr uint32_t kSmemDyn = kTiles + 1024;     // + alignment slack
+constexpr uint32_t kTmemCols = 512;             // two accumulator buffers of 256 columns
+constexpr int kProducers = 256;                  // warps 0-7
+constexpr int kEpilogue = 256;                   // warps 8-15
+static_assert(kProducers + kEpilogue == kThreads, "warp roles");
+constexpr long kWaitLimit = 1L << 26;
+
+struct TcArgs {
+  const float2 *w;
+  const float2 *y;
+  float2 *out;
+  float alpha;
+  int64_t n_items;
+  const unsigned *max_in;   // per item: largest |component| of w (float bits)
+  unsigned *max_out;        // per item: running max |component| of out
+  TcOperators ops;
+};
+
+__host__ __device__ inline uint32_t sw128_offset(int r, int c, uint32_t colblock_stride) {
+  const int j = c >> 6, cc = c & 63;
+  const uint32_t logical = (uint32_t)(r >> 3) * 1024u + (uint32_t)(r & 7) * 128u + (uint32_t)cc * 2u;
+  const uint32_t chunk = (logical >> 4) & 7u, row8 = (logical >> 7) & 7u;
+  return (uint32_t)j * colblock_stride + ((logical & ~(7u << 4)) | ((chunk ^ row8) << 4));
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// UMMA shared-memory descriptor, 128-byte swizzle, sm_100 version bits.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor: kind::f16, FP16 A and B, FP32 accumulator.
+__host__ __device__ constexpr uint32_t idesc(int M, int N, int a_mn, int b_mn, int neg_a) {
+  return (1u << 4) | ((uint32_t)neg_a << 13) | ((uint32_t)a_mn << 15) | ((uint32_t)b_mn << 16) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ uint32_t mbar_try(uint32_t addr, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n selp.b32 %0, 1, 0, P;\n}\n"
+      : "=r"(done)
+      : "r"(addr), "r"(parity));
+  return done;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.release.cta.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)));
+}
+
+// Bounded wait on an mbarrier phase; returns false (and raises the error word)
+// when the iteration limit runs out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int *abort_flag) {
+  const uint32_t addr = smem_u32(bar);
+  for (long it = 0; it < kWaitLimit; ++it) {
+    if (mbar_try(addr, parity)) return true;
+    if ((it & 1023) == 1023 && *(volatile int *)abort_flag) return false;
+  }
+  atomicExch(err, 1);
+  *(volatile int *)abort_flag = 1;
+  return false;
+}
+
+__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProducers)); }
+
+// Warp-specialised persistent stage kernel.
+//   warps 0-7  (producers): per item, two passes over w_n (max, then scale and
+//              split into the FP16 tiles); thread 0 issues the MMAs into the
+//              tensor-memory buffer of the item's parity and commits.
+//   warps 8-15 (epilogue) : per item, wait for the MMAs, read the accumulator,
+//              add decay and system-bath terms, write out; release the buffer.
+// The shared tiles are reused as soon as the item's MMAs complete, so the
+// epilogue of item k overlaps the loads and MMAs of item k + 1.
+__global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ uint64_t bar_mma[2], bar_full[2], bar_epi[2];
+  __shared__ uint32_t tmem_base;
+  __shared__ float s_scale[2];
+  __shared__ int s_abort;
+
+  const TcOperators &op = P.ops;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint8_t *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
+  uint8_t *ZZ1 = base, *ZZ2 = base + kZZ, *HT = base + 2 * kZZ;
+
+  for (uint32_t i = tid; i < 2 * kZZ / 16; i += kThreads) reinterpret_cast<uint4 *>(base)[i] = make_uint4(0, 0, 0, 0);
+  for (uint32_t i = tid; i < (uint32_t)op.n_hpieces * kHTile / 16; i += kThreads)
+    reinterpret_cast<uint4 *>(HT)[i] = op.himg[i];
+  if (tid == 0) {
+    s_abort = 0;
+    for (int t = 0; t < 2; ++t) {
+      mbar_init(&bar_mma[t], 1);
+      mbar_init(&bar_full[t], 1);
+      mbar_init(&bar_epi[t], kEpilogue / 32);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_base;
+
+  const int d = op.d, nm = op.n_modes;
+  const int64_t dd = (int64_t)d * d;
+  const int64_t n_mine = P.n_items > blockIdx.x ? (P.n_items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+  if (tid < kProducers) {
+    // ------------------------------------------------------------ producers
+    const int cp = tid & 63;           // column pair: columns 2cp, 2cp + 1
+    const int r0 = tid >> 6;           // first row; rows r0, r0 + 4, ...
+    const int c = 2 * cp;
+    const bool active = c < d;
+    const uint32_t zz[2] = {smem_u32(ZZ1), smem_u32(ZZ2)};
+    const uint32_t hh = smem_u32(HT);
+    for (int64_t k = 0; k < n_mine; ++k) {
+      const int64_t item = blockIdx.x + k * gridDim.x;
+      const int t = (int)(k & 1);
+      const float2 *wn = P.w + item * dd;
+      // warm L2 with the next item's w_n while this one is converted
+      if (k + 1 < n_mine) {
+        const char *nx = reinterpret_cast<const char *>(P.w + (item + gridDim.x) * dd);
+        for (int64_t off = (int64_t)tid * 128; off < dd * 8; off += (int64_t)kProducers * 128)
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + off));
+      }
+      // the tiles are free once the previous item's MMAs have completed; every
+      // producer reaches the barrier, then all read the abort flag (uniform exit)
+      if (k >= 1) mbar_wait(&bar_mma[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort);
+      producer_sync();
+      if (*(volatile int *)&s_abort) break;
+      // power-of-two scale from the item's largest component (kept by the previous stage)
+      const float m = __uint_as_float(P.max_in[item]);
+      float scale = 1.f;
+      if (m > 0.f && isfinite(m)) {
+        int e;
+        frexpf(m, &e);
+        scale = ldexpf(1.f, 14 - e);     // largest scaled component < 2^14
+      }
+      // pass 2: scale, split into FP16 hi + lo, store the swizzled tiles
+      if (active) {
+        for (int a8 = r0; a8 < d; a8 += 32) {
+          float2 v[16];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int a = a8 + 4 * i;
+            v[2 * i] = a < d ? wn[(int64_t)a * d + c] : make_float2(0.f, 0.f);
+            v[2 * i + 1] = (a < d && c + 1 < d) ? wn[(int64_t)a * d + c + 1] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int a = a8 + 4 * i;
+            if (a >= d) break;
+            const float xr0 = v[2 * i].x * scale, xi0 = v[2 * i].y * scale;
+            const float xr1 = v[2 * i + 1].x * scale, xi1 = v[2 * i + 1].y * scale;
+            const __half hr0 = __float2half_rn(xr0), hr1 = __float2half_rn(xr1);
+            const __half hi0 = __float2half_rn(xi0), hi1 = __float2half_rn(xi1);
+            const __half lr0 = __float2half_rn(xr0 - __half2float(hr0)), lr1 = __float2half_rn(xr1 - __half2float(hr1));
+            const __half li0 = __float2half_rn(xi0 - __half2float(hi0)), li1 = __float2half_rn(xi1 - __half2float(hi1));
+            const uint32_t ore = sw128_offset(a, c, kZZ / 2), oim = sw128_offset(a + 128, c, kZZ / 2);
+            *reinterpret_cast<__half2 *>(ZZ1 + ore) = __halves2half2(hr0, hr1);
+            *reinterpret_cast<__half2 *>(ZZ1 + oim) = __halves2half2(hi0, hi1);
+            *reinterpret_cast<__half2 *>(ZZ2 + ore) = __halves2half2(lr0, lr1);
+            *reinterpret_cast<__half2 *>(ZZ2 + oim) = __halves2half2(li0, li1);
+          }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;");
+      producer_sync();
+      if (tid == 0) {
+        // the accumulator buffer is free once the epilogue of item k - 2 released it
+        bool ok = k < 2 || mbar_wait(&bar_epi[t], (uint32_t)(((k - 2) >> 1) & 1), op.err, &s_abort);
+        s_scale[t] = scale;
+        if (ok) {
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t id_neg = idesc(128, 256, 0, 0, 1);
+          const uint32_t id_mn = idesc(128, 128, 1, 0, 0);
+          const int pj3[4] = {0, 1, 2, 0}, pk3[4] = {0, 0, 0, 1};
+          const int pj2[3] = {0, 1, 0}, pk2[3] = {0, 0, 1};
+          const int npairs = op.n_hpieces == 3 ? 4 : 3;
+          const int *pj = op.n_hpieces == 3 ? pj3 : pj2;
+          const int *pk = op.n_hpieces == 3 ? pk3 : pk2;
+          const uint32_t dcol = tmem + (uint32_t)t * 256u;
+          uint32_t acc = 0;
+          for (int q = 0; q < npairs; ++q) {
+            const uint32_t ha = hh + (uint32_t)pj[q] * kHTile, zb = zz[pk[q]];
+            for (int kk = 0; kk < 8; ++kk) {
+              const uint64_t a = sdesc(ha + (kk >> 2) * 16384u + (kk & 3) * 32u, 16, 1024);
+              const uint64_t bd = sdesc(zb + (kk >> 2) * (kZZ / 2) + (kk & 3) * 32u, 16, 1024);
+              umma(dcol, a, bd, id_neg, acc);
+              acc = 1;
+            }
+          }
+          for (int part = 0; part < 2; ++part)
+            for (int q = 0; q < npairs; ++q) {
+              const uint32_t za = zz[pk[q]] + (uint32_t)part * 16384u, hb = hh + (uint32_t)pj[q] * kHTile;
+              for (int kk = 0; kk < 8; ++kk) {
+                const uint64_t a = sdesc(za + (uint32_t)kk * 2048u, kZZ / 2, 1024);
+                const uint64_t bd = sdesc(hb + (kk >> 2) * 16384u + (kk & 3) * 32u, 16, 1024);
+                umma(dcol + (uint32_t)part * 128u, a, bd, id_mn, 1);
+              }
+            }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&bar_mma[t])));
+        }
+        mbar_arrive(&bar_full[t]);
+      }
+    }
+    // drain: the last item's MMAs must complete before the tiles and tensor memory go away
+    if (tid == 0 && n_mine > 0 && !*(volatile int *)&s_abort)
+      mbar_wait(&bar_mma[(n_mine - 1) & 1], (uint32_t)(((n_mine - 1) >> 1) & 1), op.err, &s_abort);
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int ew = warp - kProducers / 32;          // 0..7
+    const int b = 32 * (ew & 3) + lane;             // TMEM lane = column b of w_n
+    const int a_begin = 64 * (ew >> 2);
+    const uint32_t lane_field = (uint32_t)(32 * (ew & 3)) << 16;
+    for (int64_t k = 0; k < n_mine; ++k) {
+      const int64_t item = blockIdx.x + k * gridDim.x;
+      const int t = (int)(k & 1);
+      const uint32_t par = (uint32_t)((k >> 1) & 1);
+      bool ok = mbar_wait(&bar_full[t], par, op.err, &s_abort);
+      ok = ok && mbar_wait(&bar_mma[t], par, op.err, &s_abort);
+      if (!__all_sync(0xffffffffu, ok)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const int n = (int)(item % op.n_ado);
+      const float2 *wn = P.w + item * dd;
+      const float inv = op.inv_sh / s_scale[t];
+      const float dec = (float)op.decay[n];
+      float2 *ob = P.out + item * dd;
+      const uint32_t tcol = tmem + lane_field + (uint32_t)t * 256u;
+      float omax = 0.f;
+      if (k + 1 < n_mine) {   // warm L2 with the next item's out and w_n
+        const char *no = reinterpret_cast<const char *>(P.out + (item + gridDim.x) * dd);
+        const char *nw = reinterpret_cast<const char *>(P.w + (item + gridDim.x) * dd);
+        for (int64_t off = (int64_t)(tid - kProducers) * 128; off < dd * 8; off += (int64_t)kEpilogue * 128) {
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(no + off));
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(nw + off));
+        }
+      }
+      for (int a0 = a_begin; a0 < a_begin + 64 && a0 < d; a0 += 16) {
+        float are[16], aim[16];
+        {
+          uint32_t r[16];
+          tmem_ld16(tcol + (uint32_t)a0, r);
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) aim[jj] = -inv * __uint_as_float(r[jj]);
+          tmem_ld16(tcol + 128u + (uint32_t)a0, r);
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) are[jj] = inv * __uint_as_float(r[jj]);
+        }
+        if (b < d) {
+          const int na = min(16, d - a0);
+          const int64_t e0 = (int64_t)a0 * d + b;
+          float2 x[16], o[16];
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj) {
+            x[jj] = jj < na ? wn[e0 + (int64_t)jj * d] : make_float2(0.f, 0.f);
+            o[jj] = jj < na ? ob[e0 + (int64_t)jj * d] : make_float2(0.f, 0.f);
+          }
+#pragma unroll
+          for (int jj = 0; jj < 16; ++jj)
+            if (jj < na) {
+              const float2 v = make_float2(o[jj].x + P.alpha * (are[jj] - dec * x[jj].x),
+                                           o[jj].y + P.alpha * (aim[jj] - dec * x[jj].y));
+              omax = fmaxf(omax, fmaxf(fabsf(v.x), fabsf(v.y)));
+              __stcs(ob + e0 + (int64_t)jj * d, v);
+            }
+        }
+      }
+#pragma unroll
+      for (int o2 = 16; o2 > 0; o2 >>= 1) omax = fmaxf(omax, __shfl_xor_sync(0xffffffffu, omax, o2));
+      if (lane == 0) atomicMax(P.max_out + item, __float_as_uint(omax));
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_epi[t]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+}
+
+// Elementwise system-bath terms in the coupling eigenbasis (CUDA cores):
+//   out[a][b] = y[a][b] + alpha * sum_q kappa_q(a, b) w_{nb_q}[a][b],
+//   kappa_q = -i cA_q (lam_s[a_s] - lam_s[b_s]) + cB_q (lam_s[a_s] + lam_s[b_s]),
+// over the coupling list of the ADO (up- and down-neighbours of every mode).
+// One block per (item, 32-row band); thread = (column b, row parity), 16 rows
+// per thread held in registers.  The coupling list is the outer loop, so each
+// neighbour's constants are read once per block and every thread has 16
+// independent loads in flight.  No shared-memory tiles: the kernel runs at high
+// occupancy.  The block also clears the item's running maximum |out| that the
+// tensor-core kernel accumulates.
+constexpr int kVtThreads = 256;
+constexpr int kVtRowsPerThread = 16;
+constexpr int kVtRows = 2 * kVtRowsPerThread;
+constexpr int kMaxNb = 32;
+
+__global__ void __launch_bounds__(kVtThreads) vterm_kernel(const float2 *__restrict__ w, const float2 *y,
+                                                          float2 *out, float alpha, TcOperators op, int bands,
+                                                          unsigned *max_out) {
+  const int d = op.d, nm = op.n_modes;
+  const int64_t dd = (int64_t)d * d;
+  const int64_t item = blockIdx.x / bands;
+  const int band = blockIdx.x - (int)(item * bands);
+  const int n = (int)(item % op.n_ado);
+  const int64_t br = item / op.n_ado;
+  const float2 *wb = w + br * op.n_ado * dd;
+  if (threadIdx.x == 0 && band == 0 && max_out) max_out[item] = 0u;
+  const int b = threadIdx.x & 127, par = threadIdx.x >> 7;
+  if (b >= d) return;
+  const int a0 = band * kVtRows + par;          // rows a0, a0 + 2, ..., a0 + 30
+  const int nrow = min(kVtRowsPerThread, (d - a0 + 1) / 2);
+  const int64_t e0 = (int64_t)a0 * d + b, es = 2 * (int64_t)d;
+  float re[kVtRowsPerThread], im[kVtRowsPerThread];
+#pragma unroll
+  for (int j = 0; j < kVtRowsPerThread; ++j) re[j] = im[j] = 0.f;
+  const int *off = op.nb_off + n * nm;
+  for (int s = 0; s < nm; ++s) {
+    const int lo = off[s], hi = off[s + 1];
+    if (lo == hi) continue;
+    const float lb = op.lam[s * 128 + b];
+    float f[kVtRowsPerThread], g[kVtRowsPerThread];
+#pragma unroll
+    for (int j = 0; j < kVtRowsPerThread; ++j) {
+      const int a = min(a0 + 2 * j, d - 1);
+      const float la = op.lam[s * 128 + a];
+      f[j] = la - lb;
+      g[j] = la + lb;
+    }
+    for (int q = lo; q < hi; ++q) {
+      const float2 *wm = wb + (int64_t)op.nb_idx[q] * dd + e0;
+      const float cA = op.nb_cA[q], cB = op.nb_cB[q];
+      float2 x[kVtRowsPerThread];
+#pragma unroll
+      for (int j = 0; j < kVtRowsPerThread; ++j) x[j] = j < nrow ? wm[j * es] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < kVtRowsPerThread; ++j) {
+        const float pc = cB * g[j], qc = cA * f[j];
+        re[j] += pc * x[j].x + qc * x[j].y;
+        im[j] += pc * x[j].y - qc * x[j].x;
+      }
+    }
+  }
+  const float2 *yb = y + item * dd + e0;
+  float2 *ob = out + item * dd + e0;
+  float2 yv[kVtRowsPerThread];
+#pragma unroll
+  for (int j = 0; j < kVtRowsPerThread; ++j) yv[j] = j < nrow ? __ldcs(yb + j * es) : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int j = 0; j < kVtRowsPerThread; ++j)
+    if (j < nrow) ob[j * es] = make_float2(yv[j].x + alpha * re[j], yv[j].y + alpha * im[j]);
+}
+
+// Largest component magnitude of every item of a state (bit pattern of a
+// non-negative float, so integer max orders them).
+__global__ void __launch_bounds__(256) item_max_kernel(const float2 *__restrict__ x, int64_t dd, unsigned *max_out) {
+  const float2 *xi = x + (int64_t)blockIdx.x * dd;
+  float m = 0.f;
+  for (int64_t e = threadIdx.x; e < dd; e += blockDim.x) m = fmaxf(m, fmaxf(fabsf(xi[e].x), fabsf(xi[e].y)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < (int)(blockDim.x >> 5); ++i) m = fmaxf(m, red[i]);
+    max_out[blockIdx.x] = __float_as_uint(red[0] > m ? red[0] : m);
+  }
+}
+
+}  // namespace
+
+static uint16_t half_bits(double x) {
+  __half h = __double2half(x);
+  uint16_t u;
+  std::memcpy(&u, &h, 2);
+  return u;
+}
+
+static double half_value(uint16_t u) {
+  __half h;
+  std::memcpy(&h, &u, 2);
+  return (double)__half2float(h);
+}
+
+void tc_build(TcOperators &tc, const Model &M, const VbModel &vb, std::vector<void *> &allocs) {
+  const int d = M.d;
+  if (d > 128 || M.n_modes > kTcMaxModes)
+    throw std::invalid_argument("tensor-core path supports d <= 128 and at most 4 modes");
+  tc.d = d;
+  tc.n_ado = M.n_ado;
+  tc.n_modes = M.n_modes;
+  tc.n_hpieces = 3;
+  // H' shifted by a multiple of the identity (the commutator is unchanged), scaled
+  // by a power of two so the largest entry is below 2^14, split into 3 FP16 pieces.
+  double dmax = -1e300, dmin = 1e300;
+  for (int a = 0; a < d; ++a) {
+    dmax = std::max(dmax, M.vb_H[(size_t)a * d + a]);
+    dmin = std::min(dmin, M.vb_H[(size_t)a * d + a]);
+  }
+  const double shift = 0.5 * (dmax + dmin);
+  double amax = 0.0;
+  for (int a = 0; a < d; ++a)
+    for (int b2 = 0; b2 < d; ++b2) amax = std::max(amax, std::fabs(M.vb_H[(size_t)a * d + b2] - (a == b2 ? shift : 0.0)));
+  int e = 0;
+  std::frexp(amax > 0 ? amax : 1.0, &e);
+  const double sh = std::ldexp(1.0, 13 - e);
+  tc.inv_sh = (float)(1.0 / sh);
+  std::vector<uint16_t> img((size_t)3 * kHTile / 2, 0);
+  for (int a = 0; a < d; ++a)
+    for (int b2 = 0; b2 < d; ++b2) {
+      double x = (M.vb_H[(size_t)a * d + b2] - (a == b2 ? shift : 0.0)) * sh;
+      const uint32_t off = sw128_offset(a, b2, 16384) / 2;
+      for (int piece = 0; piece < 3; ++piece) {
+        const uint16_t u = half_bits(x);
+        img[(size_t)piece * kHTile / 2 + off] = u;
+        x -= half_value(u);
+      }
+    }
+  void *p = nullptr;
+  if (cudaMalloc(&p, img.size() * 2) != cudaSuccess) throw std::bad_alloc();
+  allocs.push_back(p);
+  cudaMemcpy(p, img.data(), img.size() * 2, cudaMemcpyHostToDevice);
+  tc.himg = (const uint4 *)p;
+  std::vector<float> lam((size_t)M.n_modes * 128, 0.f);
+  for (int s = 0; s < M.n_modes; ++s)
+    for (int a = 0; a < d; ++a) lam[(size_t)s * 128 + a] = (float)M.vb_lam[s][(a / M.stride[s]) % M.dims[s]];
+  if (cudaMalloc(&p, lam.size() * 4) != cudaSuccess) throw std::bad_alloc();
+  allocs.push_back(p);
+  cudaMemcpy(p, lam.data(), lam.size() * 4, cudaMemcpyHostToDevice);
+  tc.lam = (const float *)p;
+  if (cudaMalloc(&p, 16) != cudaSuccess) throw std::bad_alloc();
+  allocs.push_back(p);
+  cudaMemset(p, 0, 16);
+  tc.err = (int *)p;
+  for (int n = 0; n < M.n_ado; ++n)
+    if (M.nb_off[(size_t)n * M.n_modes + M.n_modes] - M.nb_off[(size_t)n * M.n_modes] > kMaxNb)
+      throw std::invalid_argument("tensor-core path supports at most 32 coupling entries per ADO");
+  tc.decay = vb.decay;
+  tc.nb_off = vb.nb_off;
+  tc.nb_idx = vb.nb_idx;
+  tc.nb_cA = vb.nb_cA;
+  tc.nb_cB = vb.nb_cB;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&tc.sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaFuncSetAttribute(tc_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn) != cudaSuccess)
+    throw std::invalid_argument("cannot reserve shared memory for the tensor-core stage");
+  tc.ready = true;
 }
 
 bool tc_supported(const TcOperators &tc) { return tc.ready; }
 
-void tc_rk4_steps(const TcOperators &, float2 *, float2 *, float2 *, int, double, int64_t, cudaStream_t) {
-  throw std::invalid_argument("tensor-core stage not built");
+void tc_stage(const TcOperators &tc, const float2 *w, const float2 *y, float2 *out, int branches, float alpha,
+              const unsigned *max_in, unsigned *max_out, cudaStream_t st) {
+  const int64_t n_items = (int64_t)branches * tc.n_ado;
+  const int bands = (tc.d + kVtRows - 1) / kVtRows;   // 32-row bands
+  vterm_kernel<<<(unsigned)(n_items * bands), kVtThreads, 0, st>>>(w, y, out, alpha, tc, bands, max_out);
+  count_launch(1);
+  TcArgs a;
+  a.w = w;
+  a.y = out;       // the tensor-core kernel updates out in place
+  a.out = out;
+  a.alpha = alpha;
+  a.n_items = n_items;
+  a.max_in = max_in;
+  a.max_out = max_out;
+  a.ops = tc;
+  const int grid = (int)std::min<int64_t>(n_items, tc.sms);
+  tc_stage_kernel<<<grid, kThreads, kSmemDyn, st>>>(a);
+  count_launch(1);
+}
+
+void tc_rk4_steps(TcOperators &tc, float2 *y, float2 *wa, float2 *wb, int branches, double dt, int64_t nsteps,
+                  cudaStream_t st) {
+  const int64_t n_items = (int64_t)branches * tc.n_ado;
+  if (n_items <= 0 || nsteps <= 0) return;
+  if (n_items > tc.max_items) {
+    if (tc.maxbuf) cudaFree(tc.maxbuf);
+    tc.maxbuf = nullptr;
+    tc.max_items = 0;
+    if (cudaMalloc(&tc.maxbuf, (size_t)n_items * 3 * sizeof(unsigned)) != cudaSuccess) throw std::bad_alloc();
+    tc.max_items = n_items;
+  }
+  unsigned *my = tc.maxbuf, *ma = tc.maxbuf + n_items, *mb = tc.maxbuf + 2 * n_items;
+  item_max_kernel<<<(unsigned)n_items, 256, 0, st>>>(y, (int64_t)tc.d * tc.d, my);
+  count_launch(1);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    tc_stage(tc, y, y, wa, branches, (float)(dt / 4), my, ma, st);
+    tc_stage(tc, wa, y, wb, branches, (float)(dt / 3), ma, mb, st);
+    tc_stage(tc, wb, y, wa, branches, (float)(dt / 2), mb, ma, st);
+    tc_stage(tc, wa, y, y, branches, (float)dt, ma, my, st);
+  }
 }
 
 }  // namespace heom

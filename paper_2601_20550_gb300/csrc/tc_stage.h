@@ -1,4 +1,9 @@
-// Tensor-core (tcgen05) RK4 stage for the mixed-precision path (HEOM_BF16X3).
+// Tensor-core (tcgen05) RK4 stage for the mixed-precision path (HEOM_TC).
+//
+// The state is held in the coupling eigenbasis (see kernels.cuh, VbModel): the
+// dense commutator [H', w_n] runs on the 5th-generation tensor cores with
+// split-FP16 operands (per-ADO power-of-two scaling, FP32 accumulation in
+// tensor memory) and the system-bath terms are elementwise in the epilogue.
 #pragma once
 
 #include <cstdint>
@@ -13,15 +18,32 @@ namespace heom {
 
 struct TcOperators {
   bool ready = false;
-  int d = 0, dpad = 0;
-  DevModel<float> dm{};
+  int d = 0, n_ado = 0, n_modes = 0, n_hpieces = 3;
+  float inv_sh = 1.f;             // 1 / (power-of-two scale applied to H')
+  const uint4 *himg = nullptr;    // n_hpieces shared-memory images of H' pieces (32 KB each)
+  const float *lam = nullptr;     // [n_modes][128] lam_s[digit_s(a)]
+  const double *decay = nullptr;  // [n_ado]
+  const int *nb_off = nullptr, *nb_idx = nullptr;
+  const float *nb_cA = nullptr, *nb_cB = nullptr;
+  int *err = nullptr;             // device error word (bounded waits)
+  int sms = 0;
+  unsigned *maxbuf = nullptr;     // workspace: per-item max |w| of y, wa, wb (grown on demand)
+  int64_t max_items = 0;
 };
 
-// Prepare the tensor-core operator tiles of M (device allocations are appended to allocs).
-void tc_build(TcOperators &tc, const Model &M, const DevModel<float> &dm, std::vector<void *> &allocs);
+// Prepare the tensor-core operator images of M (device allocations are appended
+// to allocs).  vb supplies the device coupling tables.  Throws std::invalid_argument
+// if the model does not fit the kernel (d > 128 or more than 4 modes).
+void tc_build(TcOperators &tc, const Model &M, const VbModel &vb, std::vector<void *> &allocs);
 bool tc_supported(const TcOperators &tc);
-// n RK4 steps (Horner form) on complex64 branches y with scratch wa, wb.
-void tc_rk4_steps(const TcOperators &tc, float2 *y, float2 *wa, float2 *wb, int branches, double dt,
+// n RK4 steps (Horner form) on complex64 coupling-basis branches y with scratch wa, wb.
+// The hierarchy keeps a workspace of three per-item maxima (12 bytes per ADO
+// per branch), grown on the first call with a larger batch.
+void tc_rk4_steps(TcOperators &tc, float2 *y, float2 *wa, float2 *wb, int branches, double dt,
                   int64_t nsteps, cudaStream_t st);
+// One stage out = y + alpha L(w): system-bath terms, then the tensor-core
+// commutator.  max_in holds the per-item max |w|; max_out receives max |out|.
+void tc_stage(const TcOperators &tc, const float2 *w, const float2 *y, float2 *out, int branches, float alpha,
+              const unsigned *max_in, unsigned *max_out, cudaStream_t st);
 
 }  // namespace heom

@@ -13,7 +13,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libheom2dvs.so")
 
-FP64, FP32, BF16X3 = 0, 1, 2
+FP64, FP32, TC = 0, 1, 2
 STATUS = {0: "HEOM_OK", -1: "HEOM_EINVAL", -2: "HEOM_ENOMEM", -3: "HEOM_ECUDA",
           -4: "HEOM_EUNSTABLE", -5: "HEOM_ETIMEOUT", -6: "HEOM_ENOTCONV",
           -7: "HEOM_ENONFINITE", -8: "HEOM_ECKPT"}
@@ -86,6 +86,8 @@ def lib():
         "heom_state_broadcast": [_P, _P],
         "heom_trace_dev": [_P, _P, ct.c_int, ct.c_int, ct.c_int, _P, _P],
         "heom_kick_dev": [_P, _P, _P, ct.c_int, ct.c_int, ct.c_int, _P],
+        "heom_state_export_dev": [_P, _P, _P],
+        "heom_state_import_dev": [_P, _P, _P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -271,6 +273,14 @@ def heom_state_broadcast(src, dst):
 
 def heom_state_device_ptr(s):
     return int(lib().heom_state_device_ptr(s.h) or 0)
+
+
+def heom_state_export_dev(s, dst_ptr, stream_ptr=0):
+    _check(lib().heom_state_export_dev(s.h, _P(dst_ptr), _P(stream_ptr)))
+
+
+def heom_state_import_dev(s, src_ptr, stream_ptr=0):
+    _check(lib().heom_state_import_dev(s.h, _P(src_ptr), _P(stream_ptr)))
 
 
 def heom_trace_dev(h, state_ptr, branches, precision, order, out_ptr, stream_ptr):

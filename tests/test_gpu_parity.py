@@ -71,6 +71,35 @@ def test_propagate_fp32():
     assert rel(got, ref) < 2e-5
 
 
+@pytest.mark.parametrize("precision", [1, 2])
+def test_propagate_coupling_basis(precision):
+    """FP32 (CUDA cores) and tensor-core paths, both in the coupling eigenbasis."""
+    model = W.small_three_mode(n=3, depth_L=2)
+    prob = OM.Problem(model)
+    h = H.heom_build_hierarchy(model, precision)
+    x = rand_state((3, prob.nado, prob.d, prob.d), 14)
+    s = H.heom_state_create(h, 3, precision)
+    H.heom_state_upload(s, x)
+    H.heom_propagate(h, s, 0.5, 4)
+    got = H.heom_state_download(s)
+    ref = OH.propagate(prob, x, 0.5, 4)
+    assert rel(got, ref) < 2e-5
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_kicks_and_trace_coupling_basis(precision):
+    model = W.small_two_mode(n1=3, n2=4, depth_L=2)
+    prob = OM.Problem(model)
+    h = H.heom_build_hierarchy(model, precision)
+    x = rand_state((2, prob.nado, prob.d, prob.d), 15)
+    s = H.heom_state_create(h, 2, precision)
+    H.heom_state_upload(s, x)
+    tr = H.heom_trace(h, s, 3)
+    assert rel(tr, (1j) ** 3 * OH.trace_mu(prob, x)) < 1e-6
+    H.heom_kick(h, s, 1)
+    assert rel(H.heom_state_download(s), OH.kick(x, prob.sys.mu_plus)) < 1e-6
+
+
 def test_kicks_and_trace():
     model = W.small_two_mode(n1=3, n2=4, depth_L=2)
     prob = OM.Problem(model)
@@ -147,6 +176,18 @@ def test_response_2d_fp32_spectrum():
     assert np.abs(SC - SCo).max() < 1e-4 * np.abs(SCo).max()
 
 
+def test_response_2d_tc_spectrum():
+    """Tensor-core path: S_C within 1e-4 of the FP64 oracle's max-norm."""
+    model = W.small_three_mode(n=3, depth_L=2)
+    grid = W.grid(0.5, 8, 24, 24, (0.0,), t_eq_fs=40.0)
+    prob = OM.Problem(model)
+    _, _, RI, RII, SC = H.spectrum_2d(model, grid, H.TC)
+    _, RIo, RIIo, SCo = OH.spectrum_2d(prob, grid)
+    scale = max(np.abs(RIo).max(), np.abs(RIIo).max())
+    assert np.abs(RI - RIo).max() < 1e-4 * scale
+    assert np.abs(SC - SCo).max() < 1e-4 * np.abs(SCo).max()
+
+
 def test_response_1d():
     model = W.harmonic_bo(omega_cm=1000.0, n_levels=8, lambda_cm=50.0, gamma_cm=200.0,
                           depth_L=2, K_pade=1)
@@ -166,6 +207,7 @@ def test_response_1d():
 @pytest.mark.parametrize("name,precision,tol,branches", [
     ("c2", 0, 1e-11, 256),
     ("c3", 1, 2e-5, 256),
+    ("c3", 2, 2e-5, 256),
 ])
 def test_full_size_batched_step_sampled(name, precision, tol, branches):
     """Full workload shape in the bench's batched launch (all branches at once),
@@ -185,16 +227,28 @@ def test_full_size_batched_step_sampled(name, precision, tol, branches):
     xs = {}
     for b in samples:
         xs[b] = rng.standard_normal((nado, d, d)) + 1j * rng.standard_normal((nado, d, d))
-        y[b].copy_(torch.from_numpy(xs[b]).to(cdt))
+        if precision == 0:
+            y[b].copy_(torch.from_numpy(xs[b]))
+        else:
+            # complex64 device states live in the coupling eigenbasis
+            st = H.heom_state_create(h, 1, precision)
+            H.heom_state_upload(st, xs[b][None])
+            H.heom_state_export_dev(st, y[b].data_ptr())
+            torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
     H.heom_propagate_dev(h, y.data_ptr(), wa.data_ptr(), wb.data_ptr(), branches, precision,
                          grid["dt_fs"], 1, stream.cuda_stream)
     torch.cuda.synchronize()
     prob = OM.Problem(model)
     for b in samples:
-        got = y[b].cpu().numpy().astype(np.complex128)
-        ref = OH.rk4_step(prob, xs[b][None].astype(np.complex64 if precision else np.complex128)
-                          .astype(np.complex128), grid["dt_fs"])[0]
+        if precision == 0:
+            got = y[b].cpu().numpy().astype(np.complex128)
+        else:
+            st = H.heom_state_create(h, 1, precision)
+            H.heom_state_import_dev(st, y[b].data_ptr())
+            torch.cuda.synchronize()
+            got = H.heom_state_download(st)[0]
+        ref = OH.rk4_step(prob, xs[b][None], grid["dt_fs"])[0]
         assert rel(got, ref) < tol
     # a branch that started at zero stays zero
     assert float(y[branches // 2].abs().max()) == 0.0

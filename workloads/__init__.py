@@ -64,18 +64,24 @@ def grid(dt_fs, m, n1, n3, t2_fs=(0.0,), t_eq_fs=200.0):
 # ---------------------------------------------------------------------------
 # Water-like three-mode model (asymmetric stretch 1, symmetric stretch 1', bend 2)
 # ---------------------------------------------------------------------------
-# Frequencies 3650 / 3750 / 1600 cm^-1.  Dipole ratios follow the linear dipole
-# column of the three-mode table (3.3 : 3.3 : 1.8 -> 1 : 1 : 0.545); the quadratic
+# Frequencies 3650 / 3750 / 1600 cm^-1; Morse depths 1e4 cm^-1 (stretches, the value
+# named for the single-mode workload) and 2e4 cm^-1 (bend).  The square-linear
+# coupling V_SL = 0.1 keeps the counter term Lambda <V^2> of the highest kept
+# stretch levels (<q^4> ~ 5e3 at 5 levels, ~3e4 at 6) small enough that the
+# Bohr-frequency spread of H_S' stays inside the RK4 stability region at the
+# workloads' dt; with V_SL = 1 the spread at 5 levels per mode is 6.2e4 cm^-1
+# (dt * spread = 5.9 at dt = 0.5 fs, beyond the RK4 limit of 2.8).
+# Dipole ratios follow the linear dipole column of the three-mode table (3.3 : 3.3 : 1.8 -> 1 : 1 : 0.545); the quadratic
 # stretch dipole is 1.2e-2 / 3.3 of the linear one; the stretch-bend dipole cross
 # terms follow the 2.0e-3 entries of the pair table on the same scale.  The cubic
 # pair couplings are drawn from numpy's default_rng(2601), U(-50, 50) cm^-1, in pair
 # order (1,1'), (1,2), (1',2), g_{s^2 s'} before g_{s s'^2} for each pair.
 WATER_OMEGA = (3650.0, 3750.0, 1600.0)
-WATER_MORSE_D = (4.0e4, 4.0e4, 2.0e4)
+WATER_MORSE_D = (1.0e4, 1.0e4, 2.0e4)
 WATER_MU1 = (1.0, 1.0, 0.545)
 WATER_MU2 = (0.0036, 0.0036, 0.0)
 WATER_PAIR_MU = {(0, 1): 0.0, (0, 2): 6.0e-4, (1, 2): 6.0e-4}
-WATER_V_SL = 0.3
+WATER_V_SL = 0.1
 WATER_V_LL = 0.1
 
 
@@ -88,11 +94,11 @@ def water_pairs(seed=2601):
     return out
 
 
-def water_model(n_levels, depth_L, K_pade=1, n_prim=240, T_K=300.0):
+def water_model(n_levels, depth_L, K_pade=1, n_prim=300, T_K=300.0):
     modes = []
     for s in range(3):
         modes.append(mode("morse", WATER_OMEGA[s], D_cm=WATER_MORSE_D[s], n_levels=n_levels,
-                          n_prim=n_prim, q_min=-5.0, q_max=11.0, V_LL=WATER_V_LL,
+                          n_prim=n_prim, q_min=-5.0, q_max=20.0, V_LL=WATER_V_LL,
                           V_SL=WATER_V_SL, mu1=WATER_MU1[s], mu2=WATER_MU2[s], K_pade=K_pade))
     return {"modes": modes, "pairs": water_pairs(), "T_K": float(T_K), "depth_L": int(depth_L)}
 
