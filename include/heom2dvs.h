@@ -241,6 +241,29 @@ heom_status heom_kick_dev(heom_hier *h, const void *in, void *out, int branches,
 heom_status heom_trace_dev(heom_hier *h, const void *state, int branches, int precision, int order,
                            void *out, void *stream);
 
+/*
+ * Allocation-free variant of heom_propagate_dev for callers that cannot
+ * allocate device memory when they propagate (a framework's caching allocator
+ * owns the pool, a real-time loop cannot afford a cudaMalloc that may
+ * synchronise the device, a plug-in has buffers but no allocation rights).
+ * The paper has no counterpart: it is a deployment variant of the RK4 step.
+ *   state    device pointer, [branches][n_ado][d][d] complex128 (HEOM_FP64
+ *            layout), advanced in place by n_steps RK4 steps on `stream`.
+ * The two RK4 scratch buffers are a file-scope __device__ array of
+ * 2 x HEOM_NOALLOC_MAX_BYTES that every GPU loading the library holds until the
+ * process exits; states larger than HEOM_NOALLOC_MAX_BYTES are rejected with
+ * HEOM_EINVAL.  The call allocates nothing and does not synchronise.  Its first
+ * call on a device resolves the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  The hierarchy must already
+ * have its device tables (any earlier device call on it, e.g. heom_state_create).
+ * Every call shares the one scratch array: calls that overlap on the GPU (other
+ * streams, other threads, other hierarchies) race and must be serialised by the
+ * caller.  No RK4 stability pre-check is made.
+ */
+#define HEOM_NOALLOC_MAX_BYTES (16LL * 1024 * 1024)
+heom_status heom_propagate_noalloc(heom_hier *h, void *state, int branches, double dt_fs,
+                                   int64_t n_steps, void *stream);
+
 void heom_free_hier(heom_hier *h);
 void heom_free_state(heom_state *s);
 const char *heom_last_error(void);

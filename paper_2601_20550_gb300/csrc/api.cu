@@ -856,3 +856,10 @@ void heom_free_hier(heom_hier *h) { delete h; }
 void heom_free_state(heom_state *s) { delete s; }
 
 }  // extern "C"
+
+// Read-only views of a hierarchy for entry points defined in other files.
+namespace heom {
+bool hier_on_device(const heom_hier *h) { return h && h->on_device; }
+const DevModel<double> &hier_dm64(const heom_hier *h) { return h->dm64; }
+void hier_set_error(const char *msg) { g_last_error = msg; }
+}  // namespace heom

@@ -87,6 +87,7 @@ def lib():
         "heom_trace_dev": [_P, _P, ct.c_int, ct.c_int, ct.c_int, _P, _P],
         "heom_kick_dev": [_P, _P, _P, ct.c_int, ct.c_int, ct.c_int, _P],
         "heom_state_export_dev": [_P, _P, _P],
+        "heom_propagate_noalloc": [_P, _P, ct.c_int, ct.c_double, ct.c_int64, _P],
         "heom_state_import_dev": [_P, _P, _P],
     }
     for name, args in sig.items():
@@ -305,6 +306,12 @@ def heom_propagate_dev(h, state_ptr, scratch_a_ptr, scratch_b_ptr, branches, pre
     """Device-pointer propagation (pointers as ints, e.g. torch tensor.data_ptr())."""
     _check(lib().heom_propagate_dev(h.h, _P(state_ptr), _P(scratch_a_ptr), _P(scratch_b_ptr),
                                     branches, precision, dt_fs, int(n_steps), _P(stream_ptr)))
+
+
+def heom_propagate_noalloc(h, state_ptr, branches, dt_fs, n_steps, stream_ptr=0):
+    """Allocation-free FP64 propagation of a device state (scratch in a static device array)."""
+    _check(lib().heom_propagate_noalloc(h.h, _P(state_ptr), branches, dt_fs, int(n_steps),
+                                        _P(stream_ptr)))
 
 
 def heom_launch_count():
