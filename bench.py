@@ -208,7 +208,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="c2-fp64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c3-mixed", choices=sorted(WORKLOADS))
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--e2e-rows", type=int, default=0, help="t1 rows per e2e step (default per workload)")
     ap.add_argument("--no-e2e", action="store_true")
