@@ -69,13 +69,14 @@ def rows_ado_updates(grid, nado, j0, j1):
 # Algorithmic cost per ADO-update of the fused stage kernel
 # ---------------------------------------------------------------------------
 def algorithmic_costs(model, d, nado, ado_table, nb_counts, prec):
-    """flops and bytes of one ADO-update (4 Horner stages), averaged over the ADOs.
+    """Algorithmic flops and bytes of one ADO-update (one ADO advanced by one RK4 step).
 
-    flops per stage: [H, w] with real H: 2 real-times-complex d^3 products = 8 d^3;
-    per mode s: neighbour sums (8 d^2 per coupling entry) and V_s applied to A_s, B_s
-    from both sides (16 d^2 n_s); decay and update (8 d^2).
-    bytes per ADO-update: 11 state passes (stage 1 reads y and writes w, stages 2-4
-    read w, y and write) of d^2 complex.
+    bytes: 20 d^2 b -- four RK4 stages, each reading the stage input, the step-start
+    state and the accumulator and writing two arrays (5 passes of d^2 complex, b = 16
+    for complex128, 8 for complex64), neighbour re-reads served from L2.
+    flops: 4 stages x ([H, w] with a real H: 8 d^3; per mode s the neighbour sums
+    (8 d^2 per coupling entry) and V_s applied to A_s, B_s from both sides
+    (16 d^2 n_s); decay and update 8 d^2).
     """
     dims = [md["n_levels"] for md in model["modes"]]
     avg_nb = nb_counts.sum(axis=0) / nado   # per mode
@@ -84,7 +85,13 @@ def algorithmic_costs(model, d, nado, ado_table, nb_counts, prec):
         stage += 8.0 * d * d * avg_nb[s] + (16.0 * d * d * n if avg_nb[s] > 0 else 0.0)
     flops = 4.0 * stage
     b = 16.0 if prec == 0 else 8.0
-    return flops, 11.0 * d * d * b
+    return flops, 20.0 * d * d * b
+
+
+# Measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per work item
+# (one ADO of one branch) of one RK4 stage of the tensor-core path, from the ncu
+# capture summarised in profiles/tc_stage_c3.md (4-branch case, scaled per item).
+TC_STAGE_TRAFFIC_BYTES_PER_ITEM = 759.4e3
 
 
 class ClockSampler:
@@ -213,6 +220,7 @@ def main():
     ap.add_argument("--e2e-rows", type=int, default=0, help="t1 rows per e2e step (default per workload)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--branches", type=int, default=0,
                     help="override the batch (profiling runs only; default 2*n1)")
     args = ap.parse_args()
@@ -311,22 +319,50 @@ def main():
     stage_launches = 4 * m * args.steps
     stage_s = prop_ms / 1000.0 / stage_launches
     per_launch_units = B * nado / 4.0       # one stage = a quarter of an ADO-update per ADO
+    # (for the tensor-core path a "stage" is the launch pair tc_stage_kernel + vterm_kernel)
     peaks, peak_kind = measured_peaks()
     if prec == 0:
         achieved = flops_upd * per_launch_units / stage_s / 1e12
         peak = 1.25
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s)",
+                "frac": achieved / peak, "traffic": None, "kernel": "stage_kernel<double>",
+                "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s); cuBLAS DGEMM measured 1.10",
                 "algorithmic_flops_per_ado_update": flops_upd}
     else:
         achieved = bytes_upd * per_launch_units / stage_s / 1e9
         peak = peaks["hbm_gbs"]
+        traffic = None
+        if prec == 2 and TC_STAGE_TRAFFIC_BYTES_PER_ITEM:
+            traffic = TC_STAGE_TRAFFIC_BYTES_PER_ITEM * B * nado
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "RK4 stage (tc_stage_kernel + vterm_kernel)" if prec == 2 else "stage_kernel_vb",
                 "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_kind,
                 "algorithmic_bytes_per_ado_update": bytes_upd,
                 "flops_TFLOPs": flops_upd * per_launch_units / stage_s / 1e12}
+
+    # ---------------- plain FP64 GPU path on the same model (mixed vs FP64) ----------------
+    fp64 = None
+    if prec != 0 and not args.no_fp64:
+        h64 = H.heom_build_hierarchy(model, 0)
+        Bf = min(B, 16)
+        s64 = H.heom_state_create(h64, Bf, 0)
+        H.heom_state_broadcast(eq, s64)
+        y64 = torch.empty((Bf, nado, d, d), dtype=torch.complex128, device=dev)
+        H.heom_kick_dev(h64, H.heom_state_device_ptr(s64), y64.data_ptr(), Bf, 0, 1, sp)
+        del s64
+        a64, b64 = torch.empty_like(y64), torch.empty_like(y64)
+        H.heom_propagate_dev(h64, y64.data_ptr(), a64.data_ptr(), b64.data_ptr(), Bf, 0, grid["dt_fs"], 1, sp)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        H.heom_propagate_dev(h64, y64.data_ptr(), a64.data_ptr(), b64.data_ptr(), Bf, 0, grid["dt_fs"], 2, sp)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        v64 = Bf * nado * 2 / (e0.elapsed_time(e1) / 1000.0)
+        fp64 = {"value": v64, "unit": "ADO-updates/s", "branches": Bf, "steps": 2,
+                "mixed_over_fp64": value / v64}
+        del y64, a64, b64, h64
 
     # ---------------- e2e through the public C ABI with host buffers ----------------
     e2e = None
@@ -375,6 +411,7 @@ def main():
             "spectra_per_hour": 3600.0 * value / per_spec,
             "ado_updates_per_spectrum": per_spec,
             "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+            "fp64_gpu": fp64,
             "gpu_launches": int(launches),
         }
         print(json.dumps(line))

@@ -200,6 +200,16 @@ heom_status heom_response_2d(heom_hier *h, const heom_state *rho_eq, const heom_
 heom_status heom_response_2d_rows(heom_hier *h, const heom_state *rho_eq, const heom_grid *g, int j0,
                                   int j1, double *R_I, double *R_II);
 
+/*
+ * 2D correlation spectrum from given responses (Eqs. 2D-rephasing,
+ * 2D-nonrephasing, correlation-spectrum), with the conventions of
+ * heom_response_2d: R_I, R_II [n_t2][n1][n3] complex on the host, t = j dtau,
+ * S_C [n_t2][n1][n3] out.  Used to assemble a spectrum from row blocks computed
+ * on several GPUs.  The Fourier sums run on the device.
+ */
+heom_status heom_spectrum_2d(const double *R_I, const double *R_II, int n_t2, int n1, int n3,
+                             double dtau_fs, double *S_C);
+
 /* Copy branch 0 of src into every branch of dst (converting precision). */
 heom_status heom_state_broadcast(const heom_state *src, heom_state *dst);
 

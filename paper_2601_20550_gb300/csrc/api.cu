@@ -754,6 +754,29 @@ heom_status heom_response_2d_rows(heom_hier *h, const heom_state *rho_eq, const 
   });
 }
 
+heom_status heom_spectrum_2d(const double *R_I, const double *R_II, int n_t2, int n1, int n3, double dtau_fs,
+                             double *S_C) {
+  if (!R_I || !R_II || !S_C || n_t2 < 1 || n1 < 1 || n3 < 1 || !(dtau_fs > 0))
+    return fail(HEOM_EINVAL, "bad spectrum arguments");
+  return guarded([&]() -> heom_status {
+    const size_t blk = (size_t)n1 * n3;
+    DeviceBuffer R((size_t)n_t2 * 2 * blk * 16), S((size_t)n_t2 * blk * 8);
+    for (int it = 0; it < n_t2; ++it) {
+      CUDA_TRY(cudaMemcpy((char *)R.p + (size_t)it * 2 * blk * 16, R_I + it * blk * 2, blk * 16, cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpy((char *)R.p + ((size_t)it * 2 + 1) * blk * 16, R_II + it * blk * 2, blk * 16,
+                          cudaMemcpyHostToDevice));
+    }
+    for (int it = 0; it < n_t2; ++it) {
+      const double2 *RI = (const double2 *)R.p + (size_t)it * 2 * blk;
+      dft2d_sc_kernel<<<(unsigned)((blk + 255) / 256), 256>>>(RI, RI + blk, n1, n3, dtau_fs, (double *)S.p + it * blk);
+      count_launch(1);
+      LAUNCH_CHECK();
+    }
+    CUDA_TRY(cudaMemcpy(S_C, S.p, S.bytes, cudaMemcpyDeviceToHost));
+    return HEOM_OK;
+  });
+}
+
 heom_status heom_state_broadcast(const heom_state *src, heom_state *dst) {
   if (!src || !dst || src->d != dst->d || src->n_ado != dst->n_ado) return fail(HEOM_EINVAL, "bad broadcast arguments");
   return guarded([&]() -> heom_status {

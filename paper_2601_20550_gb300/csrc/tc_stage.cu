@@ -10,10 +10,10 @@
 //      H' pieces (hi, mid, lo) resident in shared memory, FP32 accumulation in
 //      tensor memory (256 columns: Re D | Im D);
 //   3. the epilogue reads D from tensor memory (lane = column b of w_n, column =
-//      row a) and updates out += alpha * (-i C - gamma_n w_n) with coalesced
-//      accesses.  The elementwise system-bath terms are written into out before
-//      by vterm_kernel (out = y + alpha * sum kappa w_nb), a streaming kernel that
-//      runs at full occupancy so that enough neighbour loads are in flight.
+//      row a) and updates out += alpha * (-i C) with coalesced accesses.  The
+//      elementwise terms are written into out before by vterm_kernel
+//      (out = y + alpha * (-gamma_n w_n + sum kappa w_nb)), a streaming kernel
+//      that runs at high occupancy so that enough neighbour loads are in flight.
 // All waits are bounded: on expiry the kernel sets the error word, frees its
 // tensor memory and returns.
 #include "tc_stage.h"
@@ -38,8 +38,8 @@ constexpr uint32_t kZZ = 65536;                  // 256 x 128 FP16 (re | im rows
 constexpr uint32_t kTiles = 2 * kZZ + 3 * kHTile;
 constexpr uint32_t kSmemDyn = kTiles + 1024;     // + alignment slack
 constexpr uint32_t kTmemCols = 512;             // two accumulator buffers of 256 columns
-constexpr int kProducers = 256;                  // warps 0-7
-constexpr int kEpilogue = 256;                   // warps 8-15
+constexpr int kProducers = 384;                  // warps 0-11
+constexpr int kEpilogue = 128;                   // warps 12-15
 static_assert(kProducers + kEpilogue == kThreads, "warp roles");
 constexpr long kWaitLimit = 1L << 26;
 
@@ -97,6 +97,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
+}
+
+// TMA bulk prefetch of [p, p + bytes) into L2, restricted to its 16-byte-aligned
+// interior (a prefetch need not cover every byte).
+__device__ __forceinline__ void l2_prefetch_bulk(const void *p, int64_t bytes) {
+  uint64_t lo = ((uint64_t)p + 15u) & ~(uint64_t)15u;
+  const uint64_t hi = ((uint64_t)p + (uint64_t)bytes) & ~(uint64_t)15u;
+  while (lo < hi) {
+    const uint32_t n = (uint32_t)((hi - lo) < (1u << 16) ? (hi - lo) : (1u << 16));
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"(n) : "memory");
+    lo += n;
+  }
 }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
@@ -164,14 +176,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
 
-  const int d = op.d, nm = op.n_modes;
+  const int d = op.d;
   const int64_t dd = (int64_t)d * d;
   const int64_t n_mine = P.n_items > blockIdx.x ? (P.n_items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
   if (tid < kProducers) {
     // ------------------------------------------------------------ producers
     const int cp = tid & 63;           // column pair: columns 2cp, 2cp + 1
-    const int r0 = tid >> 6;           // first row; rows r0, r0 + 4, ...
+    const int r0 = tid >> 6;           // first row; rows r0, r0 + 6, ...
     const int c = 2 * cp;
     const bool active = c < d;
     const uint32_t zz[2] = {smem_u32(ZZ1), smem_u32(ZZ2)};
@@ -180,12 +192,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       const int64_t item = blockIdx.x + k * gridDim.x;
       const int t = (int)(k & 1);
       const float2 *wn = P.w + item * dd;
-      // warm L2 with the next item's w_n while this one is converted
-      if (k + 1 < n_mine) {
-        const char *nx = reinterpret_cast<const char *>(P.w + (item + gridDim.x) * dd);
-        for (int64_t off = (int64_t)tid * 128; off < dd * 8; off += (int64_t)kProducers * 128)
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(nx + off));
-      }
+      // warm L2 with the next item's w_n while this one is converted (one bulk prefetch)
+      if (k + 1 < n_mine && tid == 0) l2_prefetch_bulk(P.w + (item + gridDim.x) * dd, dd * 8);
       // the tiles are free once the previous item's MMAs have completed; every
       // producer reaches the barrier, then all read the abort flag (uniform exit)
       if (k >= 1) mbar_wait(&bar_mma[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort);
@@ -199,19 +207,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
         frexpf(m, &e);
         scale = ldexpf(1.f, 14 - e);     // largest scaled component < 2^14
       }
-      // pass 2: scale, split into FP16 hi + lo, store the swizzled tiles
+      // scale, split into FP16 hi + lo, store the swizzled tiles (12 rows per batch)
       if (active) {
-        for (int a8 = r0; a8 < d; a8 += 32) {
-          float2 v[16];
+        for (int ab = r0; ab < d; ab += 72) {
+          float2 v[24];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int a = a8 + 4 * i;
-            v[2 * i] = a < d ? wn[(int64_t)a * d + c] : make_float2(0.f, 0.f);
-            v[2 * i + 1] = (a < d && c + 1 < d) ? wn[(int64_t)a * d + c + 1] : make_float2(0.f, 0.f);
+          for (int i = 0; i < 12; ++i) {
+            const int a = min(ab + 6 * i, d - 1);
+            v[2 * i] = wn[(int64_t)a * d + c];
+            v[2 * i + 1] = c + 1 < d ? wn[(int64_t)a * d + c + 1] : make_float2(0.f, 0.f);
           }
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int a = a8 + 4 * i;
+          for (int i = 0; i < 12; ++i) {
+            const int a = ab + 6 * i;
             if (a >= d) break;
             const float xr0 = v[2 * i].x * scale, xi0 = v[2 * i].y * scale;
             const float xr1 = v[2 * i + 1].x * scale, xi1 = v[2 * i + 1].y * scale;
@@ -273,10 +281,9 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       mbar_wait(&bar_mma[(n_mine - 1) & 1], (uint32_t)(((n_mine - 1) >> 1) & 1), op.err, &s_abort);
   } else {
     // ------------------------------------------------------------ epilogue
-    const int ew = warp - kProducers / 32;          // 0..7
-    const int b = 32 * (ew & 3) + lane;             // TMEM lane = column b of w_n
-    const int a_begin = 64 * (ew >> 2);
-    const uint32_t lane_field = (uint32_t)(32 * (ew & 3)) << 16;
+    const int ew = warp - kProducers / 32;          // 0..3: TMEM lane quadrant
+    const int b = 32 * ew + lane;                   // TMEM lane = column b of w_n
+    const uint32_t lane_field = (uint32_t)(32 * ew) << 16;
     for (int64_t k = 0; k < n_mine; ++k) {
       const int64_t item = blockIdx.x + k * gridDim.x;
       const int t = (int)(k & 1);
@@ -285,56 +292,25 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       ok = ok && mbar_wait(&bar_mma[t], par, op.err, &s_abort);
       if (!__all_sync(0xffffffffu, ok)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const int n = (int)(item % op.n_ado);
-      const float2 *wn = P.w + item * dd;
-      const float inv = op.inv_sh / s_scale[t];
-      const float dec = (float)op.decay[n];
+      // out = alpha * (-i C); the system-bath kernel adds y and the rest next
+      if (tid == kProducers) P.max_out[item] = 0u;
+      const float sc = P.alpha * op.inv_sh / s_scale[t];
       float2 *ob = P.out + item * dd;
       const uint32_t tcol = tmem + lane_field + (uint32_t)t * 256u;
-      float omax = 0.f;
-      if (k + 1 < n_mine) {   // warm L2 with the next item's out and w_n
-        const char *no = reinterpret_cast<const char *>(P.out + (item + gridDim.x) * dd);
-        const char *nw = reinterpret_cast<const char *>(P.w + (item + gridDim.x) * dd);
-        for (int64_t off = (int64_t)(tid - kProducers) * 128; off < dd * 8; off += (int64_t)kEpilogue * 128) {
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(no + off));
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(nw + off));
-        }
-      }
-      for (int a0 = a_begin; a0 < a_begin + 64 && a0 < d; a0 += 16) {
-        float are[16], aim[16];
-        {
-          uint32_t r[16];
-          tmem_ld16(tcol + (uint32_t)a0, r);
-          asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) aim[jj] = -inv * __uint_as_float(r[jj]);
-          tmem_ld16(tcol + 128u + (uint32_t)a0, r);
-          asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) are[jj] = inv * __uint_as_float(r[jj]);
-        }
+      for (int a0 = 0; a0 < d; a0 += 16) {
+        uint32_t rr[16], ri[16];
+        tmem_ld16(tcol + (uint32_t)a0, rr);
+        tmem_ld16(tcol + 128u + (uint32_t)a0, ri);
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
         if (b < d) {
-          const int na = min(16, d - a0);
           const int64_t e0 = (int64_t)a0 * d + b;
-          float2 x[16], o[16];
-#pragma unroll
-          for (int jj = 0; jj < 16; ++jj) {
-            x[jj] = jj < na ? wn[e0 + (int64_t)jj * d] : make_float2(0.f, 0.f);
-            o[jj] = jj < na ? ob[e0 + (int64_t)jj * d] : make_float2(0.f, 0.f);
-          }
 #pragma unroll
           for (int jj = 0; jj < 16; ++jj)
-            if (jj < na) {
-              const float2 v = make_float2(o[jj].x + P.alpha * (are[jj] - dec * x[jj].x),
-                                           o[jj].y + P.alpha * (aim[jj] - dec * x[jj].y));
-              omax = fmaxf(omax, fmaxf(fabsf(v.x), fabsf(v.y)));
-              __stcs(ob + e0 + (int64_t)jj * d, v);
-            }
+            if (a0 + jj < d)
+              __stcg(ob + e0 + (int64_t)jj * d,
+                     make_float2(sc * __uint_as_float(ri[jj]), -sc * __uint_as_float(rr[jj])));
         }
       }
-#pragma unroll
-      for (int o2 = 16; o2 > 0; o2 >>= 1) omax = fmaxf(omax, __shfl_xor_sync(0xffffffffu, omax, o2));
-      if (lane == 0) atomicMax(P.max_out + item, __float_as_uint(omax));
       asm volatile("tcgen05.fence::before_thread_sync;");
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar_epi[t]);
@@ -345,24 +321,24 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
 }
 
-// Elementwise system-bath terms in the coupling eigenbasis (CUDA cores):
-//   out[a][b] = y[a][b] + alpha * sum_q kappa_q(a, b) w_{nb_q}[a][b],
+// Elementwise terms in the coupling eigenbasis (CUDA cores): decay and system-bath
+//   out[a][b] = y[a][b] + alpha * (-gamma_n w_n[a][b] + sum_q kappa_q(a, b) w_{nb_q}[a][b]),
 //   kappa_q = -i cA_q (lam_s[a_s] - lam_s[b_s]) + cB_q (lam_s[a_s] + lam_s[b_s]),
 // over the coupling list of the ADO (up- and down-neighbours of every mode).
-// One block per (item, 32-row band); thread = (column b, row parity), 16 rows
+// One block per (item, 16-row band); thread = (column b, row parity), 8 rows
 // per thread held in registers.  The coupling list is the outer loop, so each
 // neighbour's constants are read once per block and every thread has 16
 // independent loads in flight.  No shared-memory tiles: the kernel runs at high
 // occupancy.  The block also clears the item's running maximum |out| that the
 // tensor-core kernel accumulates.
 constexpr int kVtThreads = 256;
-constexpr int kVtRowsPerThread = 16;
+constexpr int kVtRowsPerThread = 8;
 constexpr int kVtRows = 2 * kVtRowsPerThread;
 constexpr int kMaxNb = 32;
 
 __global__ void __launch_bounds__(kVtThreads) vterm_kernel(const float2 *__restrict__ w, const float2 *y,
-                                                          float2 *out, float alpha, TcOperators op, int bands,
-                                                          unsigned *max_out) {
+                                                          const float2 *tpart, float2 *out, float alpha,
+                                                          TcOperators op, int bands, unsigned *max_out) {
   const int d = op.d, nm = op.n_modes;
   const int64_t dd = (int64_t)d * d;
   const int64_t item = blockIdx.x / bands;
@@ -370,11 +346,11 @@ __global__ void __launch_bounds__(kVtThreads) vterm_kernel(const float2 *__restr
   const int n = (int)(item % op.n_ado);
   const int64_t br = item / op.n_ado;
   const float2 *wb = w + br * op.n_ado * dd;
-  if (threadIdx.x == 0 && band == 0 && max_out) max_out[item] = 0u;
   const int b = threadIdx.x & 127, par = threadIdx.x >> 7;
-  if (b >= d) return;
-  const int a0 = band * kVtRows + par;          // rows a0, a0 + 2, ..., a0 + 30
-  const int nrow = min(kVtRowsPerThread, (d - a0 + 1) / 2);
+  const int a0 = band * kVtRows + par;          // rows a0, a0 + 2, ..., a0 + 14
+  // lanes past the last column keep running (no loads or stores) so that the
+  // warp-wide maximum below sees every lane
+  const int nrow = b < d ? max(0, min(kVtRowsPerThread, (d - a0 + 1) / 2)) : 0;
   const int64_t e0 = (int64_t)a0 * d + b, es = 2 * (int64_t)d;
   float re[kVtRowsPerThread], im[kVtRowsPerThread];
 #pragma unroll
@@ -406,14 +382,39 @@ __global__ void __launch_bounds__(kVtThreads) vterm_kernel(const float2 *__restr
       }
     }
   }
-  const float2 *yb = y + item * dd + e0;
-  float2 *ob = out + item * dd + e0;
-  float2 yv[kVtRowsPerThread];
+  {  // decay: - gamma_n w_n
+    const float dec = (float)op.decay[n];
+    const float2 *wn = wb + (int64_t)n * dd + e0;
+    float2 x[kVtRowsPerThread];
 #pragma unroll
-  for (int j = 0; j < kVtRowsPerThread; ++j) yv[j] = j < nrow ? __ldcs(yb + j * es) : make_float2(0.f, 0.f);
+    for (int j = 0; j < kVtRowsPerThread; ++j) x[j] = j < nrow ? wn[j * es] : make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < kVtRowsPerThread; ++j) {
+      re[j] -= dec * x[j].x;
+      im[j] -= dec * x[j].y;
+    }
+  }
+  const float2 *yb = y + item * dd + e0;
+  const float2 *tb = tpart + item * dd + e0;
+  float2 *ob = out + item * dd + e0;
+  float2 yv[kVtRowsPerThread], tv[kVtRowsPerThread];
+#pragma unroll
+  for (int j = 0; j < kVtRowsPerThread; ++j) {
+    yv[j] = j < nrow ? __ldcs(yb + j * es) : make_float2(0.f, 0.f);
+    tv[j] = j < nrow ? __ldcs(tb + j * es) : make_float2(0.f, 0.f);
+  }
+  float omax = 0.f;
 #pragma unroll
   for (int j = 0; j < kVtRowsPerThread; ++j)
-    if (j < nrow) ob[j * es] = make_float2(yv[j].x + alpha * re[j], yv[j].y + alpha * im[j]);
+    if (j < nrow) {
+      const float2 v = make_float2(yv[j].x + tv[j].x + alpha * re[j], yv[j].y + tv[j].y + alpha * im[j]);
+      omax = fmaxf(omax, fmaxf(fabsf(v.x), fabsf(v.y)));
+      ob[j * es] = v;
+    }
+  // running max |out| of the item (the tensor-core kernel cleared it)
+#pragma unroll
+  for (int o2 = 16; o2 > 0; o2 >>= 1) omax = fmaxf(omax, __shfl_xor_sync(0xffffffffu, omax, o2));
+  if ((threadIdx.x & 31) == 0 && max_out) atomicMax(max_out + item, __float_as_uint(omax));
 }
 
 // Largest component magnitude of every item of a state (bit pattern of a
@@ -516,16 +517,13 @@ void tc_build(TcOperators &tc, const Model &M, const VbModel &vb, std::vector<vo
 
 bool tc_supported(const TcOperators &tc) { return tc.ready; }
 
-void tc_stage(const TcOperators &tc, const float2 *w, const float2 *y, float2 *out, int branches, float alpha,
-              const unsigned *max_in, unsigned *max_out, cudaStream_t st) {
+void tc_stage(const TcOperators &tc, const float2 *w, const float2 *y, float2 *out, float2 *tpart, int branches,
+              float alpha, const unsigned *max_in, unsigned *max_out, cudaStream_t st) {
   const int64_t n_items = (int64_t)branches * tc.n_ado;
-  const int bands = (tc.d + kVtRows - 1) / kVtRows;   // 32-row bands
-  vterm_kernel<<<(unsigned)(n_items * bands), kVtThreads, 0, st>>>(w, y, out, alpha, tc, bands, max_out);
-  count_launch(1);
   TcArgs a;
   a.w = w;
-  a.y = out;       // the tensor-core kernel updates out in place
-  a.out = out;
+  a.y = y;
+  a.out = tpart;   // alpha * (-i [H', w]) goes to tpart first
   a.alpha = alpha;
   a.n_items = n_items;
   a.max_in = max_in;
@@ -533,7 +531,9 @@ void tc_stage(const TcOperators &tc, const float2 *w, const float2 *y, float2 *o
   a.ops = tc;
   const int grid = (int)std::min<int64_t>(n_items, tc.sms);
   tc_stage_kernel<<<grid, kThreads, kSmemDyn, st>>>(a);
-  count_launch(1);
+  const int bands = (tc.d + kVtRows - 1) / kVtRows;   // 16-row bands
+  vterm_kernel<<<(unsigned)(n_items * bands), kVtThreads, 0, st>>>(w, y, tpart, out, alpha, tc, bands, max_out);
+  count_launch(2);
 }
 
 void tc_rk4_steps(TcOperators &tc, float2 *y, float2 *wa, float2 *wb, int branches, double dt, int64_t nsteps,
@@ -551,10 +551,12 @@ void tc_rk4_steps(TcOperators &tc, float2 *y, float2 *wa, float2 *wb, int branch
   item_max_kernel<<<(unsigned)n_items, 256, 0, st>>>(y, (int64_t)tc.d * tc.d, my);
   count_launch(1);
   for (int64_t s = 0; s < nsteps; ++s) {
-    tc_stage(tc, y, y, wa, branches, (float)(dt / 4), my, ma, st);
-    tc_stage(tc, wa, y, wb, branches, (float)(dt / 3), ma, mb, st);
-    tc_stage(tc, wb, y, wa, branches, (float)(dt / 2), mb, ma, st);
-    tc_stage(tc, wa, y, y, branches, (float)dt, ma, my, st);
+    // the tensor-core part of a stage goes to a buffer that is neither y nor w:
+    // out itself in stages 1-3, the free scratch wb in stage 4 (out = y there)
+    tc_stage(tc, y, y, wa, wa, branches, (float)(dt / 4), my, ma, st);
+    tc_stage(tc, wa, y, wb, wb, branches, (float)(dt / 3), ma, mb, st);
+    tc_stage(tc, wb, y, wa, wa, branches, (float)(dt / 2), mb, ma, st);
+    tc_stage(tc, wa, y, y, wb, branches, (float)dt, ma, my, st);
   }
 }
 

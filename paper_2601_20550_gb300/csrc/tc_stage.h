@@ -41,9 +41,11 @@ bool tc_supported(const TcOperators &tc);
 // per branch), grown on the first call with a larger batch.
 void tc_rk4_steps(TcOperators &tc, float2 *y, float2 *wa, float2 *wb, int branches, double dt,
                   int64_t nsteps, cudaStream_t st);
-// One stage out = y + alpha L(w): system-bath terms, then the tensor-core
-// commutator.  max_in holds the per-item max |w|; max_out receives max |out|.
-void tc_stage(const TcOperators &tc, const float2 *w, const float2 *y, float2 *out, int branches, float alpha,
-              const unsigned *max_in, unsigned *max_out, cudaStream_t st);
+// One stage out = y + alpha L(w): the tensor-core kernel writes
+// tpart = alpha (-i [H', w]) (tpart may equal out but not y or w), then the
+// streaming kernel writes out = y + tpart + alpha (-gamma w + sum kappa w_nb).
+// max_in holds the per-item max |w|; max_out receives max |out|.
+void tc_stage(const TcOperators &tc, const float2 *w, const float2 *y, float2 *out, float2 *tpart, int branches,
+              float alpha, const unsigned *max_in, unsigned *max_out, cudaStream_t st);
 
 }  // namespace heom

@@ -84,6 +84,7 @@ def lib():
         "heom_propagate_dev": [_P, _P, _P, _P, ct.c_int, ct.c_int, ct.c_double, ct.c_int64, _P],
         "heom_response_2d_rows": [_P, _P, ct.POINTER(heom_grid), ct.c_int, ct.c_int, _D, _D],
         "heom_state_broadcast": [_P, _P],
+        "heom_spectrum_2d": [_D, _D, ct.c_int, ct.c_int, ct.c_int, ct.c_double, _D],
         "heom_trace_dev": [_P, _P, ct.c_int, ct.c_int, ct.c_int, _P, _P],
         "heom_kick_dev": [_P, _P, _P, ct.c_int, ct.c_int, ct.c_int, _P],
         "heom_state_export_dev": [_P, _P, _P],
@@ -266,6 +267,16 @@ def heom_response_2d_rows(h, rho_eq, grid, j0, j1):
     _check(lib().heom_response_2d_rows(h.h, rho_eq.h, ct.byref(g), j0, j1, RI.ctypes.data_as(_D),
                                        RII.ctypes.data_as(_D)))
     return RI, RII
+
+
+def heom_spectrum_2d(R_I, R_II, dtau_fs):
+    """S_C from R_I, R_II of shape (n_t2, n1, n3) (device Fourier sums)."""
+    RI = np.ascontiguousarray(R_I, dtype=np.complex128)
+    RII = np.ascontiguousarray(R_II, dtype=np.complex128)
+    SC = np.zeros(RI.shape)
+    _check(lib().heom_spectrum_2d(RI.ctypes.data_as(_D), RII.ctypes.data_as(_D), RI.shape[0],
+                                  RI.shape[1], RI.shape[2], dtau_fs, SC.ctypes.data_as(_D)))
+    return SC
 
 
 def heom_state_broadcast(src, dst):
