@@ -40,6 +40,7 @@ constexpr uint32_t kSmemDyn = kTiles + 1024;     // + alignment slack
 constexpr uint32_t kTmemCols = 512;             // two accumulator buffers of 256 columns
 constexpr int kProducers = 384;                  // warps 0-11
 constexpr int kEpilogue = 128;                   // warps 12-15
+constexpr int kProdRows = 12;                    // rows per producer batch (2 batches cover 144 >= 128 rows)
 static_assert(kProducers + kEpilogue == kThreads, "warp roles");
 constexpr long kWaitLimit = 1L << 26;
 
@@ -144,7 +145,7 @@ __device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, %0;"
 // epilogue of item k overlaps the loads and MMAs of item k + 1.
 __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t bar_mma[2], bar_full[2], bar_epi[2];
+  __shared__ uint64_t bar_mma[2], bar_lo[2], bar_full[2], bar_epi[2];
   __shared__ uint32_t tmem_base;
   __shared__ float s_scale[2];
   __shared__ int s_abort;
@@ -161,6 +162,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
     s_abort = 0;
     for (int t = 0; t < 2; ++t) {
       mbar_init(&bar_mma[t], 1);
+      mbar_init(&bar_lo[t], 1);
       mbar_init(&bar_full[t], 1);
       mbar_init(&bar_epi[t], kEpilogue / 32);
     }
@@ -194,9 +196,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       const float2 *wn = P.w + item * dd;
       // warm L2 with the next item's w_n while this one is converted (one bulk prefetch)
       if (k + 1 < n_mine && tid == 0) l2_prefetch_bulk(P.w + (item + gridDim.x) * dd, dd * 8);
-      // the tiles are free once the previous item's MMAs have completed; every
-      // producer reaches the barrier, then all read the abort flag (uniform exit)
-      if (k >= 1) mbar_wait(&bar_mma[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort);
+      // The lo tiles are free once the previous item's first MMA group (the
+      // products with Z2) has completed; every producer reaches the barrier, then
+      // all read the abort flag (uniform exit).
+      if (k >= 1) mbar_wait(&bar_lo[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort);
       producer_sync();
       if (*(volatile int *)&s_abort) break;
       // power-of-two scale from the item's largest component (kept by the previous stage)
@@ -207,36 +210,53 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
         frexpf(m, &e);
         scale = ldexpf(1.f, 14 - e);     // largest scaled component < 2^14
       }
-      // scale, split into FP16 hi + lo, store the swizzled tiles (12 rows per batch)
-      if (active) {
-        for (int ab = r0; ab < d; ab += 72) {
-          float2 v[24];
+      // scale and split into FP16 hi + lo; lo goes to the tiles now, hi is kept in
+      // registers until the previous item's remaining MMAs (with Z1) are done
+      __half2 hre[2 * kProdRows], him[2 * kProdRows];
 #pragma unroll
-          for (int i = 0; i < 12; ++i) {
-            const int a = min(ab + 6 * i, d - 1);
-            v[2 * i] = wn[(int64_t)a * d + c];
-            v[2 * i + 1] = c + 1 < d ? wn[(int64_t)a * d + c + 1] : make_float2(0.f, 0.f);
-          }
+      for (int bt = 0; bt < 2; ++bt) {
+        const int ab = r0 + 6 * kProdRows * bt;
+        float2 v[2 * kProdRows];
 #pragma unroll
-          for (int i = 0; i < 12; ++i) {
-            const int a = ab + 6 * i;
-            if (a >= d) break;
-            const float xr0 = v[2 * i].x * scale, xi0 = v[2 * i].y * scale;
-            const float xr1 = v[2 * i + 1].x * scale, xi1 = v[2 * i + 1].y * scale;
-            const __half hr0 = __float2half_rn(xr0), hr1 = __float2half_rn(xr1);
-            const __half hi0 = __float2half_rn(xi0), hi1 = __float2half_rn(xi1);
+        for (int i = 0; i < kProdRows; ++i) {
+          const int a = min(ab + 6 * i, d - 1);
+          v[2 * i] = active ? wn[(int64_t)a * d + c] : make_float2(0.f, 0.f);
+          v[2 * i + 1] = (active && c + 1 < d) ? wn[(int64_t)a * d + c + 1] : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < kProdRows; ++i) {
+          const int a = ab + 6 * i;
+          const float xr0 = v[2 * i].x * scale, xi0 = v[2 * i].y * scale;
+          const float xr1 = v[2 * i + 1].x * scale, xi1 = v[2 * i + 1].y * scale;
+          const __half hr0 = __float2half_rn(xr0), hr1 = __float2half_rn(xr1);
+          const __half hi0 = __float2half_rn(xi0), hi1 = __float2half_rn(xi1);
+          hre[kProdRows * bt + i] = __halves2half2(hr0, hr1);
+          him[kProdRows * bt + i] = __halves2half2(hi0, hi1);
+          if (active && a < d) {
             const __half lr0 = __float2half_rn(xr0 - __half2float(hr0)), lr1 = __float2half_rn(xr1 - __half2float(hr1));
             const __half li0 = __float2half_rn(xi0 - __half2float(hi0)), li1 = __float2half_rn(xi1 - __half2float(hi1));
-            const uint32_t ore = sw128_offset(a, c, kZZ / 2), oim = sw128_offset(a + 128, c, kZZ / 2);
-            *reinterpret_cast<__half2 *>(ZZ1 + ore) = __halves2half2(hr0, hr1);
-            *reinterpret_cast<__half2 *>(ZZ1 + oim) = __halves2half2(hi0, hi1);
-            *reinterpret_cast<__half2 *>(ZZ2 + ore) = __halves2half2(lr0, lr1);
-            *reinterpret_cast<__half2 *>(ZZ2 + oim) = __halves2half2(li0, li1);
+            *reinterpret_cast<__half2 *>(ZZ2 + sw128_offset(a, c, kZZ / 2)) = __halves2half2(lr0, lr1);
+            *reinterpret_cast<__half2 *>(ZZ2 + sw128_offset(a + 128, c, kZZ / 2)) = __halves2half2(li0, li1);
           }
         }
       }
+      // the hi tiles are free once the previous item's MMAs have all completed
+      if (k >= 1) mbar_wait(&bar_mma[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort);
+      if (active) {
+#pragma unroll
+        for (int bt = 0; bt < 2; ++bt)
+#pragma unroll
+          for (int i = 0; i < kProdRows; ++i) {
+            const int a = r0 + 6 * kProdRows * bt + 6 * i;
+            if (a < d) {
+              *reinterpret_cast<__half2 *>(ZZ1 + sw128_offset(a, c, kZZ / 2)) = hre[kProdRows * bt + i];
+              *reinterpret_cast<__half2 *>(ZZ1 + sw128_offset(a + 128, c, kZZ / 2)) = him[kProdRows * bt + i];
+            }
+          }
+      }
       asm volatile("fence.proxy.async.shared::cta;");
       producer_sync();
+      if (*(volatile int *)&s_abort) break;
       if (tid == 0) {
         // the accumulator buffer is free once the epilogue of item k - 2 released it
         bool ok = k < 2 || mbar_wait(&bar_epi[t], (uint32_t)(((k - 2) >> 1) & 1), op.err, &s_abort);
@@ -245,31 +265,33 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
           asm volatile("tcgen05.fence::after_thread_sync;");
           const uint32_t id_neg = idesc(128, 256, 0, 0, 1);
           const uint32_t id_mn = idesc(128, 128, 1, 0, 0);
-          const int pj3[4] = {0, 1, 2, 0}, pk3[4] = {0, 0, 0, 1};
-          const int pj2[3] = {0, 1, 0}, pk2[3] = {0, 0, 1};
-          const int npairs = op.n_hpieces == 3 ? 4 : 3;
-          const int *pj = op.n_hpieces == 3 ? pj3 : pj2;
-          const int *pk = op.n_hpieces == 3 ? pk3 : pk2;
+          // products kept by the split: H1 Z2 first (it frees the lo tiles), then
+          // H1 Z1 + H2 Z1 (+ H3 Z1) with the hi tiles
           const uint32_t dcol = tmem + (uint32_t)t * 256u;
-          uint32_t acc = 0;
-          for (int q = 0; q < npairs; ++q) {
-            const uint32_t ha = hh + (uint32_t)pj[q] * kHTile, zb = zz[pk[q]];
-            for (int kk = 0; kk < 8; ++kk) {
-              const uint64_t a = sdesc(ha + (kk >> 2) * 16384u + (kk & 3) * 32u, 16, 1024);
-              const uint64_t bd = sdesc(zb + (kk >> 2) * (kZZ / 2) + (kk & 3) * 32u, 16, 1024);
-              umma(dcol, a, bd, id_neg, acc);
-              acc = 1;
-            }
-          }
-          for (int part = 0; part < 2; ++part)
-            for (int q = 0; q < npairs; ++q) {
-              const uint32_t za = zz[pk[q]] + (uint32_t)part * 16384u, hb = hh + (uint32_t)pj[q] * kHTile;
+          const int nh = op.n_hpieces;
+          for (int grp = 0; grp < 2; ++grp) {
+            const int zk = grp == 0 ? 1 : 0;                 // Z piece of this group
+            const int j_lo = 0, j_hi = grp == 0 ? 1 : nh;     // H pieces of this group
+            for (int j = j_lo; j < j_hi; ++j) {
+              const uint32_t ha = hh + (uint32_t)j * kHTile, zb = zz[zk];
               for (int kk = 0; kk < 8; ++kk) {
-                const uint64_t a = sdesc(za + (uint32_t)kk * 2048u, kZZ / 2, 1024);
-                const uint64_t bd = sdesc(hb + (kk >> 2) * 16384u + (kk & 3) * 32u, 16, 1024);
-                umma(dcol + (uint32_t)part * 128u, a, bd, id_mn, 1);
+                const uint64_t a = sdesc(ha + (kk >> 2) * 16384u + (kk & 3) * 32u, 16, 1024);
+                const uint64_t bd = sdesc(zb + (kk >> 2) * (kZZ / 2) + (kk & 3) * 32u, 16, 1024);
+                umma(dcol, a, bd, id_neg, (grp | j | kk) ? 1u : 0u);
+              }
+              for (int part = 0; part < 2; ++part) {
+                const uint32_t za = zz[zk] + (uint32_t)part * 16384u;
+                for (int kk = 0; kk < 8; ++kk) {
+                  const uint64_t a = sdesc(za + (uint32_t)kk * 2048u, kZZ / 2, 1024);
+                  const uint64_t bd = sdesc(ha + (kk >> 2) * 16384u + (kk & 3) * 32u, 16, 1024);
+                  umma(dcol + (uint32_t)part * 128u, a, bd, id_mn, 1);
+                }
               }
             }
+            if (grp == 0)
+              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  smem_u32(&bar_lo[t])));
+          }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
               smem_u32(&bar_mma[t])));
         }
@@ -409,7 +431,7 @@ __global__ void __launch_bounds__(kVtThreads) vterm_kernel(const float2 *__restr
     if (j < nrow) {
       const float2 v = make_float2(yv[j].x + tv[j].x + alpha * re[j], yv[j].y + tv[j].y + alpha * im[j]);
       omax = fmaxf(omax, fmaxf(fabsf(v.x), fabsf(v.y)));
-      ob[j * es] = v;
+      __stcs(ob + j * es, v);
     }
   // running max |out| of the item (the tensor-core kernel cleared it)
 #pragma unroll
