@@ -192,6 +192,15 @@ heom_status heom_response_2d(heom_hier *h, const heom_state *rho_eq, const heom_
                              double *R_I, double *R_II, double *S_C);
 
 /*
+ * Several parameter sets (hierarchies of any basis size, each with its own
+ * single-branch FP64 equilibrium) on one grid: outputs [n_sets][n_t2][n1][n3]
+ * with the layouts of heom_response_2d (any output may be NULL).  Sets run one
+ * after the other, each with all its branches batched.
+ */
+heom_status heom_response_2d_batched(heom_hier *const *hs, const heom_state *const *eqs, int n_sets,
+                                     const heom_grid *g, double *R_I, double *R_II, double *S_C);
+
+/*
  * Rows j0 <= j < j1 (t1 = j m dt) of R_I and R_II only, into R_I, R_II
  * [n_t2][j1 - j0][n3] complex (either may be NULL).  The union of row ranges is
  * the full response; row blocks are independent (the unit of work sharding).

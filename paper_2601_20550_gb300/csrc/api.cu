@@ -245,6 +245,38 @@ static void trace_into(heom_hier *h, const typename CxT<R>::type *w, int branche
 // ---------------------------------------------------------------------------
 // 2D response (Sec. II.C.2) in precision R.
 // ---------------------------------------------------------------------------
+// Stream capture of a launch sequence into a CUDA graph, replayed once by
+// replay().  If an exception leaves the scope during capture, the capture is
+// ended and discarded so the stream is usable again.
+struct GraphCapture {
+  cudaStream_t st;
+  bool capturing = false;
+  explicit GraphCapture(cudaStream_t s) : st(s) {
+    CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    capturing = true;
+  }
+  void replay() {
+    cudaGraph_t g = nullptr;
+    capturing = false;
+    CUDA_TRY(cudaStreamEndCapture(st, &g));
+    cudaGraphExec_t ex = nullptr;
+    cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(ex, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (ex) cudaGraphExecDestroy(ex);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) throw Fail{HEOM_ECUDA, std::string("graph replay: ") + cudaGetErrorString(e)};
+  }
+  ~GraphCapture() {
+    if (capturing) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(st, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+    }
+  }
+};
+
 // Original-basis complex128 ADOs -> coupling-basis complex64 (U^T x U), and back.
 static void to_coupling_basis(heom_hier *h, const double2 *x, float2 *out, int64_t elems, cudaStream_t st) {
   DeviceBuffer tmp(elems * 16);
@@ -328,12 +360,16 @@ static void response_2d_rows_impl(heom_hier *h, const heom_state *eq, const heom
       LAUNCH_CHECK();
     }
     int64_t t_now = 0;
+    if (sizeof(R) == 4 && M.precision == HEOM_TC) tc_reserve(h->tc, (int64_t)B * M.n_ado);
     for (int oi = 0; oi < nt2; ++oi) {
       const int it = order[oi];
       C *Y = (C *)P1.p, *WA = (C *)P2.p, *WB = (C *)(nsets == 4 ? P3.p : P0.p);
       rk4_steps<R>(h, BR, Y, WA, B, dt, n2[it] - t_now, st, M.precision);
       t_now = n2[it];
       kick_into<R>(h, BR, Y, B, 1, st);
+      // the t3 scan (n3 samples of m RK4 steps and two traces) is captured once
+      // into a CUDA graph and replayed as a single launch
+      GraphCapture cap(st);
       for (int k = 0; k < n3; ++k) {
         if (k > 0) rk4_steps<R>(h, Y, WA, WB, B, dt, m, st, M.precision);
         for (int pw = 0; pw < 2; ++pw) {
@@ -341,6 +377,7 @@ static void response_2d_rows_impl(heom_hier *h, const heom_state *eq, const heom
           trace_into<R>(h, Y + (int64_t)pw * nj * per_branch, nj, 3, base, n3, st);
         }
       }
+      cap.replay();
     }
   }
 }
@@ -724,6 +761,18 @@ heom_status heom_response_2d(heom_hier *h, const heom_state *rho_eq, const heom_
       if (!std::isfinite(v)) throw Fail{HEOM_ENONFINITE, "response is not finite"};
     return HEOM_OK;
   });
+}
+
+heom_status heom_response_2d_batched(heom_hier *const *hs, const heom_state *const *eqs, int n_sets,
+                                     const heom_grid *g, double *R_I, double *R_II, double *S_C) {
+  if (!hs || !eqs || !g || n_sets < 1) return fail(HEOM_EINVAL, "bad batched arguments");
+  const size_t blk = (size_t)g->n_t2 * g->n1 * g->n3;
+  for (int i = 0; i < n_sets; ++i) {
+    heom_status st = heom_response_2d(hs[i], eqs[i], g, R_I ? R_I + i * blk * 2 : nullptr,
+                                      R_II ? R_II + i * blk * 2 : nullptr, S_C ? S_C + i * blk : nullptr);
+    if (st != HEOM_OK) return st;
+  }
+  return HEOM_OK;
 }
 
 heom_status heom_response_2d_rows(heom_hier *h, const heom_state *rho_eq, const heom_grid *g, int j0, int j1,

@@ -558,18 +558,21 @@ void tc_stage(const TcOperators &tc, const float2 *w, const float2 *y, float2 *o
   count_launch(2);
 }
 
+void tc_reserve(TcOperators &tc, int64_t n_items) {
+  if (n_items <= tc.max_items) return;
+  if (tc.maxbuf) cudaFree(tc.maxbuf);
+  tc.maxbuf = nullptr;
+  tc.max_items = 0;
+  if (cudaMalloc(&tc.maxbuf, (size_t)n_items * 3 * sizeof(unsigned)) != cudaSuccess) throw std::bad_alloc();
+  tc.max_items = n_items;
+}
+
 void tc_rk4_steps(TcOperators &tc, float2 *y, float2 *wa, float2 *wb, int branches, double dt, int64_t nsteps,
                   cudaStream_t st) {
   const int64_t n_items = (int64_t)branches * tc.n_ado;
   if (n_items <= 0 || nsteps <= 0) return;
-  if (n_items > tc.max_items) {
-    if (tc.maxbuf) cudaFree(tc.maxbuf);
-    tc.maxbuf = nullptr;
-    tc.max_items = 0;
-    if (cudaMalloc(&tc.maxbuf, (size_t)n_items * 3 * sizeof(unsigned)) != cudaSuccess) throw std::bad_alloc();
-    tc.max_items = n_items;
-  }
-  unsigned *my = tc.maxbuf, *ma = tc.maxbuf + n_items, *mb = tc.maxbuf + 2 * n_items;
+  tc_reserve(tc, n_items);
+  unsigned *my = tc.maxbuf, *ma = tc.maxbuf + tc.max_items, *mb = tc.maxbuf + 2 * tc.max_items;
   item_max_kernel<<<(unsigned)n_items, 256, 0, st>>>(y, (int64_t)tc.d * tc.d, my);
   count_launch(1);
   for (int64_t s = 0; s < nsteps; ++s) {

@@ -41,6 +41,8 @@ bool tc_supported(const TcOperators &tc);
 // per branch), grown on the first call with a larger batch.
 void tc_rk4_steps(TcOperators &tc, float2 *y, float2 *wa, float2 *wb, int branches, double dt,
                   int64_t nsteps, cudaStream_t st);
+// Grow the per-item maxima workspace to n_items (outside any stream capture).
+void tc_reserve(TcOperators &tc, int64_t n_items);
 // One stage out = y + alpha L(w): the tensor-core kernel writes
 // tpart = alpha (-i [H', w]) (tpart may equal out but not y or w), then the
 // streaming kernel writes out = y + tpart + alpha (-gamma w + sum kappa w_nb).

@@ -83,6 +83,7 @@ def lib():
         "heom_response_1d": [_P, _P, ct.c_double, ct.c_int, ct.c_int, _D, _D],
         "heom_propagate_dev": [_P, _P, _P, _P, ct.c_int, ct.c_int, ct.c_double, ct.c_int64, _P],
         "heom_response_2d_rows": [_P, _P, ct.POINTER(heom_grid), ct.c_int, ct.c_int, _D, _D],
+        "heom_response_2d_batched": [ct.POINTER(_P), ct.POINTER(_P), ct.c_int, ct.POINTER(heom_grid), _D, _D, _D],
         "heom_state_broadcast": [_P, _P],
         "heom_spectrum_2d": [_D, _D, ct.c_int, ct.c_int, ct.c_int, ct.c_double, _D],
         "heom_trace_dev": [_P, _P, ct.c_int, ct.c_int, ct.c_int, _P, _P],
@@ -256,6 +257,21 @@ def heom_response_2d(h, rho_eq, grid):
     SC = np.zeros(shape)
     _check(lib().heom_response_2d(h.h, rho_eq.h, ct.byref(g), RI.ctypes.data_as(_D),
                                   RII.ctypes.data_as(_D), SC.ctypes.data_as(_D)))
+    return RI, RII, SC
+
+
+def heom_response_2d_batched(hiers, eqs, grid):
+    """R_I, R_II, S_C of shape (n_sets, n_t2, n1, n3) for several parameter sets."""
+    g = marshal_grid(grid)
+    n = len(hiers)
+    shape = (n, len(grid["t2_fs"]), grid["n1"], grid["n3"])
+    RI = np.zeros(shape, dtype=np.complex128)
+    RII = np.zeros(shape, dtype=np.complex128)
+    SC = np.zeros(shape)
+    harr = (_P * n)(*[x.h for x in hiers])
+    earr = (_P * n)(*[x.h for x in eqs])
+    _check(lib().heom_response_2d_batched(harr, earr, n, ct.byref(g), RI.ctypes.data_as(_D),
+                                          RII.ctypes.data_as(_D), SC.ctypes.data_as(_D)))
     return RI, RII, SC
 
 

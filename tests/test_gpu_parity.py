@@ -272,3 +272,33 @@ def test_rows_and_spectrum_assembly():
     assert np.abs(RII - RIIo).max() < 1e-10 * scale
     SC = H.heom_spectrum_2d(RI, RII, grid["dt_fs"] * grid["steps_per_sample"])
     assert np.abs(SC - SCo).max() < 1e-10 * np.abs(SCo).max()
+
+
+def test_response_2d_batched_parameter_sets():
+    """Two parameter sets of different basis size on one grid, in one call."""
+    grid = W.grid(0.5, 3, 5, 6, (0.0, 3.0), t_eq_fs=20.0)
+    models = [W.small_two_mode(n1=3, n2=3, depth_L=2), W.small_three_mode(n=2, depth_L=2)]
+    hs = [H.heom_build_hierarchy(m) for m in models]
+    eqs = [H.heom_equilibrate(h, grid["dt_fs"], grid["t_eq_fs"], 0.0) for h in hs]
+    RI, RII, SC = H.heom_response_2d_batched(hs, eqs, grid)
+    assert RI.shape == (2, 2, 5, 6)
+    for i, m in enumerate(models):
+        _, RIo, RIIo, SCo = OH.spectrum_2d(OM.Problem(m), grid)
+        scale = max(np.abs(RIo).max(), np.abs(RIIo).max())
+        assert np.abs(RI[i] - RIo).max() < 1e-10 * scale
+        assert np.abs(RII[i] - RIIo).max() < 1e-10 * scale
+        assert np.abs(SC[i] - SCo).max() < 1e-10 * np.abs(SCo).max()
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-10), (2, 1e-4)])
+@pytest.mark.parametrize("n1,n3,depth_L", [(1, 1, 2), (1, 7, 2), (6, 1, 2), (4, 5, 0)])
+def test_response_2d_degenerate_grids(precision, tol, n1, n3, depth_L):
+    """Single-sample axes and the zero-depth hierarchy (no bath auxiliaries)."""
+    model = W.small_two_mode(n1=3, n2=3, depth_L=depth_L)
+    grid = W.grid(0.5, 3, n1, n3, (0.0,), t_eq_fs=15.0)
+    _, _, RI, RII, SC = H.spectrum_2d(model, grid, precision)
+    _, RIo, RIIo, SCo = OH.spectrum_2d(OM.Problem(model), grid)
+    scale = max(np.abs(RIo).max(), np.abs(RIIo).max())
+    assert np.abs(RI - RIo).max() < tol * scale
+    assert np.abs(RII - RIIo).max() < tol * scale
+    assert np.abs(SC - SCo).max() <= tol * np.abs(SCo).max() + 1e-300
