@@ -245,6 +245,8 @@ heom_status heom_response_1d(heom_hier *h, const heom_state *rho_eq, double dt_f
  * HEOM_FP64 in the product eigenbasis; complex64 in the coupling eigenbasis
  * otherwise), row-major, ADO stride d*d.  No allocation, no synchronisation;
  * the result is in state.  HEOM_TC requires a hierarchy built with HEOM_TC.
+ * Buffers must be aligned to their complex element (16 or 8 bytes; HEOM_EINVAL
+ * otherwise).
  */
 heom_status heom_propagate_dev(heom_hier *h, void *state, void *scratch_a, void *scratch_b,
                                int branches, int precision, double dt_fs, int64_t n_steps,

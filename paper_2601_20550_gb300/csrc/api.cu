@@ -605,6 +605,8 @@ heom_status heom_propagate_dev(heom_hier *h, void *state, void *scratch_a, void 
                                int precision, double dt_fs, int64_t n_steps, void *stream) {
   if (!h || !state || !scratch_a || !scratch_b || branches < 1 || n_steps < 0 || precision < 0 || precision > 2)
     return fail(HEOM_EINVAL, "bad propagate_dev arguments");
+  if ((((uintptr_t)state | (uintptr_t)scratch_a | (uintptr_t)scratch_b) & (precision == HEOM_FP64 ? 15u : 7u)))
+    return fail(HEOM_EINVAL, "state buffers must be aligned to their complex element size");
   return guarded([&]() -> heom_status {
     ensure_device(h);
     stability_check(h, dt_fs);

@@ -1,19 +1,22 @@
 // Tensor-core (tcgen05) RK4 stage of the HEOM right-hand side (Eq. HEOM_DB) for
-// the mixed-precision path, sm_103a.
+// the mixed-precision path, sm_103a.  A stage out = y + alpha L(w) runs as two
+// kernels.
 //
-// One persistent CTA per SM walks the work items (branch, ADO).  For each item:
-//   1. all 256 threads load w_n (complex64, d x d) from HBM, find its largest
-//      component, scale it by a power of two into FP16 range and split every
-//      component into hi + lo FP16 parts, written to shared memory in the
-//      128-byte-swizzled UMMA layout (re rows 0..127, im rows 128..255);
+// tc_stage_kernel: one persistent CTA per SM walks the work items (branch, ADO):
+//   1. producer warps 0-11 load w_n (complex64, d x d), scale it by the power of
+//      two taken from its largest component (tracked by the previous stage) into
+//      FP16 range and split every component into hi + lo FP16 parts, written to
+//      shared memory in the 128-byte-swizzled UMMA layout (re rows 0..127, im
+//      rows 128..255; hi tiles ZZ1, lo tiles ZZ2);
 //   2. one thread issues tcgen05.mma: D = Z^T H' - H' Z^T = [H', Z]^T with the
-//      H' pieces (hi, mid, lo) resident in shared memory, FP32 accumulation in
-//      tensor memory (256 columns: Re D | Im D);
-//   3. the epilogue reads D from tensor memory (lane = column b of w_n, column =
-//      row a) and updates out += alpha * (-i C) with coalesced accesses.  The
-//      elementwise terms are written into out before by vterm_kernel
-//      (out = y + alpha * (-gamma_n w_n + sum kappa w_nb)), a streaming kernel
-//      that runs at high occupancy so that enough neighbour loads are in flight.
+//      H' pieces (hi, mid, lo) resident in shared memory and FP32 accumulation in
+//      tensor memory (256 columns: Re D | Im D, double-buffered), in two commit
+//      groups so the lo tiles are released before the hi products finish;
+//   3. epilogue warps 12-15 read D from tensor memory (lane = column b of w_n,
+//      column = row a) and store tpart = alpha (-i C) with coalesced accesses.
+// vterm_kernel then adds y, tpart and the elementwise decay and system-bath
+// terms (out = y + tpart + alpha (-gamma_n w_n + sum kappa w_nb)) as a streaming
+// kernel at high occupancy, so that enough neighbour loads are in flight.
 // All waits are bounded: on expiry the kernel sets the error word, frees its
 // tensor memory and returns.
 #include "tc_stage.h"
@@ -136,13 +139,14 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
 __device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProducers)); }
 
 // Warp-specialised persistent stage kernel.
-//   warps 0-7  (producers): per item, two passes over w_n (max, then scale and
-//              split into the FP16 tiles); thread 0 issues the MMAs into the
-//              tensor-memory buffer of the item's parity and commits.
-//   warps 8-15 (epilogue) : per item, wait for the MMAs, read the accumulator,
-//              add decay and system-bath terms, write out; release the buffer.
-// The shared tiles are reused as soon as the item's MMAs complete, so the
-// epilogue of item k overlaps the loads and MMAs of item k + 1.
+//   warps 0-11 (producers): per item, wait until the previous item's first MMA
+//              group has released the lo tiles, load and split w_n (lo parts to
+//              the tiles, hi parts held in registers), wait for the remaining
+//              MMAs, write the hi parts; thread 0 then issues the item's MMAs
+//              into the tensor-memory buffer of the item's parity and commits.
+//   warps 12-15 (epilogue): per item, wait for the MMAs, read the accumulator,
+//              store tpart and release the buffer.
+// The epilogue of item k overlaps the loads and MMAs of item k + 1.
 __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t bar_mma[2], bar_lo[2], bar_full[2], bar_epi[2];
@@ -188,6 +192,18 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
     const int r0 = tid >> 6;           // first row; rows r0, r0 + 6, ...
     const int c = 2 * cp;
     const bool active = c < d;
+    // byte offsets of this thread's __half2 in the 128B-swizzled tiles: row a of a
+    // 64-column block sits at 128 a, its 16-byte chunk (c mod 64) / 8 is XORed with
+    // a mod 8.  Rows a = r0 + 6 g repeat a mod 8 every 4 steps of g (6 * 4 = 24),
+    // so four offsets plus a multiple of 4 * 6 * 128 = 3072 bytes cover all rows
+    // (the imaginary half, rows a + 128, adds 16384).
+    uint32_t row_ofs[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int a = r0 + 6 * u, cc = c & 63;
+      row_ofs[u] = (uint32_t)(c >> 6) * (kZZ / 2) + (uint32_t)a * 128u +
+                   ((uint32_t)((cc >> 3) ^ (a & 7)) << 4) + (uint32_t)((cc * 2) & 15);
+    }
     const uint32_t zz[2] = {smem_u32(ZZ1), smem_u32(ZZ2)};
     const uint32_t hh = smem_u32(HT);
     for (int64_t k = 0; k < n_mine; ++k) {
@@ -225,18 +241,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
         }
 #pragma unroll
         for (int i = 0; i < kProdRows; ++i) {
-          const int a = ab + 6 * i;
-          const float xr0 = v[2 * i].x * scale, xi0 = v[2 * i].y * scale;
-          const float xr1 = v[2 * i + 1].x * scale, xi1 = v[2 * i + 1].y * scale;
-          const __half hr0 = __float2half_rn(xr0), hr1 = __float2half_rn(xr1);
-          const __half hi0 = __float2half_rn(xi0), hi1 = __float2half_rn(xi1);
-          hre[kProdRows * bt + i] = __halves2half2(hr0, hr1);
-          him[kProdRows * bt + i] = __halves2half2(hi0, hi1);
-          if (active && a < d) {
-            const __half lr0 = __float2half_rn(xr0 - __half2float(hr0)), lr1 = __float2half_rn(xr1 - __half2float(hr1));
-            const __half li0 = __float2half_rn(xi0 - __half2float(hi0)), li1 = __float2half_rn(xi1 - __half2float(hi1));
-            *reinterpret_cast<__half2 *>(ZZ2 + sw128_offset(a, c, kZZ / 2)) = __halves2half2(lr0, lr1);
-            *reinterpret_cast<__half2 *>(ZZ2 + sw128_offset(a + 128, c, kZZ / 2)) = __halves2half2(li0, li1);
+          const int g = kProdRows * bt + i;                  // row a = r0 + 6 g
+          const float2 xr = make_float2(v[2 * i].x * scale, v[2 * i + 1].x * scale);
+          const float2 xi = make_float2(v[2 * i].y * scale, v[2 * i + 1].y * scale);
+          const __half2 hr = __float22half2_rn(xr), hi = __float22half2_rn(xi);
+          hre[g] = hr;
+          him[g] = hi;
+          if (active && r0 + 6 * g < d) {
+            const float2 fr = __half22float2(hr), fi = __half22float2(hi);
+            const uint32_t o = row_ofs[g & 3] + 3072u * (uint32_t)(g >> 2);
+            *reinterpret_cast<__half2 *>(ZZ2 + o) = __float22half2_rn(make_float2(xr.x - fr.x, xr.y - fr.y));
+            *reinterpret_cast<__half2 *>(ZZ2 + o + 16384u) = __float22half2_rn(make_float2(xi.x - fi.x, xi.y - fi.y));
           }
         }
       }
@@ -244,14 +259,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       if (k >= 1) mbar_wait(&bar_mma[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort);
       if (active) {
 #pragma unroll
-        for (int bt = 0; bt < 2; ++bt)
-#pragma unroll
-          for (int i = 0; i < kProdRows; ++i) {
-            const int a = r0 + 6 * kProdRows * bt + 6 * i;
-            if (a < d) {
-              *reinterpret_cast<__half2 *>(ZZ1 + sw128_offset(a, c, kZZ / 2)) = hre[kProdRows * bt + i];
-              *reinterpret_cast<__half2 *>(ZZ1 + sw128_offset(a + 128, c, kZZ / 2)) = him[kProdRows * bt + i];
-            }
+        for (int g = 0; g < 2 * kProdRows; ++g)
+          if (r0 + 6 * g < d) {
+            const uint32_t o = row_ofs[g & 3] + 3072u * (uint32_t)(g >> 2);
+            *reinterpret_cast<__half2 *>(ZZ1 + o) = hre[g];
+            *reinterpret_cast<__half2 *>(ZZ1 + o + 16384u) = him[g];
           }
       }
       asm volatile("fence.proxy.async.shared::cta;");
@@ -344,15 +356,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
 }
 
 // Elementwise terms in the coupling eigenbasis (CUDA cores): decay and system-bath
-//   out[a][b] = y[a][b] + alpha * (-gamma_n w_n[a][b] + sum_q kappa_q(a, b) w_{nb_q}[a][b]),
+//   out[a][b] = y[a][b] + tpart[a][b]
+//             + alpha * (-gamma_n w_n[a][b] + sum_q kappa_q(a, b) w_{nb_q}[a][b]),
 //   kappa_q = -i cA_q (lam_s[a_s] - lam_s[b_s]) + cB_q (lam_s[a_s] + lam_s[b_s]),
 // over the coupling list of the ADO (up- and down-neighbours of every mode).
 // One block per (item, 16-row band); thread = (column b, row parity), 8 rows
 // per thread held in registers.  The coupling list is the outer loop, so each
-// neighbour's constants are read once per block and every thread has 16
-// independent loads in flight.  No shared-memory tiles: the kernel runs at high
-// occupancy.  The block also clears the item's running maximum |out| that the
-// tensor-core kernel accumulates.
+// neighbour's constants are read once per block and every thread has 8
+// independent loads in flight per neighbour.  No shared-memory tiles: the kernel
+// runs at high occupancy.  The block raises the item's running maximum |out|,
+// which the tensor-core kernel cleared, with one atomic per warp.
 constexpr int kVtThreads = 256;
 constexpr int kVtRowsPerThread = 8;
 constexpr int kVtRows = 2 * kVtRowsPerThread;
