@@ -8,10 +8,11 @@
 //      FP16 range and split every component into hi + lo FP16 parts, written to
 //      shared memory in the 128-byte-swizzled UMMA layout (re rows 0..127, im
 //      rows 128..255; hi tiles ZZ1, lo tiles ZZ2);
-//   2. one thread issues tcgen05.mma: D = Z^T H' - H' Z^T = [H', Z]^T with the
-//      H' pieces (hi, mid, lo) resident in shared memory and FP32 accumulation in
-//      tensor memory (256 columns: Re D | Im D, double-buffered), in two commit
-//      groups so the lo tiles are released before the hi products finish;
+//   2. one thread of warp 16 issues tcgen05.mma: D = Z^T H' - H' Z^T = [H', Z]^T
+//      with the H' pieces (hi, mid, lo) resident in shared memory and FP32
+//      accumulation in tensor memory (256 columns: Re D | Im D, double-buffered),
+//      in two commit groups so the lo tiles are released before the hi products
+//      finish;
 //   3. epilogue warps 12-15 read D from tensor memory (lane = column b of w_n,
 //      column = row a) and store tpart = alpha (-i C) with coalesced accesses.
 // vterm_kernel then adds y, tpart and the elementwise decay and system-bath
@@ -34,7 +35,7 @@ void count_launch(uint64_t n);
 
 namespace {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 544;
 constexpr int kTcMaxModes = 4;
 constexpr uint32_t kHTile = 32768;               // 128 x 128 FP16
 constexpr uint32_t kZZ = 65536;                  // 256 x 128 FP16 (re | im rows)
@@ -43,8 +44,9 @@ constexpr uint32_t kSmemDyn = kTiles + 1024;     // + alignment slack
 constexpr uint32_t kTmemCols = 512;             // two accumulator buffers of 256 columns
 constexpr int kProducers = 384;                  // warps 0-11
 constexpr int kEpilogue = 128;                   // warps 12-15
+constexpr int kMmaWarp = 16;                     // warp 16: tensor-core issue
 constexpr int kProdRows = 12;                    // rows per producer batch (2 batches cover 144 >= 128 rows)
-static_assert(kProducers + kEpilogue == kThreads, "warp roles");
+static_assert(kProducers + kEpilogue + 32 == kThreads, "warp roles");
 constexpr long kWaitLimit = 1L << 26;
 
 struct TcArgs {
@@ -138,20 +140,36 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
 
 __device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProducers)); }
 
+// Power-of-two scale that brings an item's largest component (float bits m)
+// below 2^14; producers and epilogue derive it from the same word.
+__device__ __forceinline__ float item_scale(unsigned mbits) {
+  const float m = __uint_as_float(mbits);
+  float scale = 1.f;
+  if (m > 0.f && isfinite(m)) {
+    int e;
+    frexpf(m, &e);
+    scale = ldexpf(1.f, 14 - e);
+  }
+  return scale;
+}
+
 // Warp-specialised persistent stage kernel.
 //   warps 0-11 (producers): per item, wait until the previous item's first MMA
 //              group has released the lo tiles, load and split w_n (lo parts to
 //              the tiles, hi parts held in registers), wait for the remaining
-//              MMAs, write the hi parts; thread 0 then issues the item's MMAs
-//              into the tensor-memory buffer of the item's parity and commits.
+//              MMAs, write the hi parts and signal the tiles ready.
+//   warp 16    (MMA issue): per item, wait for the tiles and for the
+//              tensor-memory buffer of the item's parity, issue the MMAs in two
+//              commit groups.  Issue blocks while the tensor cores drain the
+//              queue, so it runs in its own warp and the producers convert the
+//              next item meanwhile.
 //   warps 12-15 (epilogue): per item, wait for the MMAs, read the accumulator,
 //              store tpart and release the buffer.
-// The epilogue of item k overlaps the loads and MMAs of item k + 1.
+// The epilogue of item k overlaps the MMAs of item k + 1 and the loads of k + 2.
 __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t bar_mma[2], bar_lo[2], bar_full[2], bar_epi[2];
+  __shared__ uint64_t bar_mma[2], bar_lo[2], bar_full[2], bar_epi[2], bar_ready[2];
   __shared__ uint32_t tmem_base;
-  __shared__ float s_scale[2];
   __shared__ int s_abort;
 
   const TcOperators &op = P.ops;
@@ -169,6 +187,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       mbar_init(&bar_lo[t], 1);
       mbar_init(&bar_full[t], 1);
       mbar_init(&bar_epi[t], kEpilogue / 32);
+      mbar_init(&bar_ready[t], kProducers / 32);
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -204,8 +223,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       row_ofs[u] = (uint32_t)(c >> 6) * (kZZ / 2) + (uint32_t)a * 128u +
                    ((uint32_t)((cc >> 3) ^ (a & 7)) << 4) + (uint32_t)((cc * 2) & 15);
     }
-    const uint32_t zz[2] = {smem_u32(ZZ1), smem_u32(ZZ2)};
-    const uint32_t hh = smem_u32(HT);
     for (int64_t k = 0; k < n_mine; ++k) {
       const int64_t item = blockIdx.x + k * gridDim.x;
       const int t = (int)(k & 1);
@@ -219,13 +236,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       producer_sync();
       if (*(volatile int *)&s_abort) break;
       // power-of-two scale from the item's largest component (kept by the previous stage)
-      const float m = __uint_as_float(P.max_in[item]);
-      float scale = 1.f;
-      if (m > 0.f && isfinite(m)) {
-        int e;
-        frexpf(m, &e);
-        scale = ldexpf(1.f, 14 - e);     // largest scaled component < 2^14
-      }
+      const float scale = item_scale(P.max_in[item]);
       // scale and split into FP16 hi + lo; lo goes to the tiles now, hi is kept in
       // registers until the previous item's remaining MMAs (with Z1) are done
       __half2 hre[2 * kProdRows], him[2 * kProdRows];
@@ -267,53 +278,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
           }
       }
       asm volatile("fence.proxy.async.shared::cta;");
-      producer_sync();
-      if (*(volatile int *)&s_abort) break;
-      if (tid == 0) {
-        // the accumulator buffer is free once the epilogue of item k - 2 released it
-        bool ok = k < 2 || mbar_wait(&bar_epi[t], (uint32_t)(((k - 2) >> 1) & 1), op.err, &s_abort);
-        s_scale[t] = scale;
-        if (ok) {
-          asm volatile("tcgen05.fence::after_thread_sync;");
-          const uint32_t id_neg = idesc(128, 256, 0, 0, 1);
-          const uint32_t id_mn = idesc(128, 128, 1, 0, 0);
-          // products kept by the split: H1 Z2 first (it frees the lo tiles), then
-          // H1 Z1 + H2 Z1 (+ H3 Z1) with the hi tiles
-          const uint32_t dcol = tmem + (uint32_t)t * 256u;
-          const int nh = op.n_hpieces;
-          for (int grp = 0; grp < 2; ++grp) {
-            const int zk = grp == 0 ? 1 : 0;                 // Z piece of this group
-            const int j_lo = 0, j_hi = grp == 0 ? 1 : nh;     // H pieces of this group
-            for (int j = j_lo; j < j_hi; ++j) {
-              const uint32_t ha = hh + (uint32_t)j * kHTile, zb = zz[zk];
-              for (int kk = 0; kk < 8; ++kk) {
-                const uint64_t a = sdesc(ha + (kk >> 2) * 16384u + (kk & 3) * 32u, 16, 1024);
-                const uint64_t bd = sdesc(zb + (kk >> 2) * (kZZ / 2) + (kk & 3) * 32u, 16, 1024);
-                umma(dcol, a, bd, id_neg, (grp | j | kk) ? 1u : 0u);
-              }
-              for (int part = 0; part < 2; ++part) {
-                const uint32_t za = zz[zk] + (uint32_t)part * 16384u;
-                for (int kk = 0; kk < 8; ++kk) {
-                  const uint64_t a = sdesc(za + (uint32_t)kk * 2048u, kZZ / 2, 1024);
-                  const uint64_t bd = sdesc(ha + (kk >> 2) * 16384u + (kk & 3) * 32u, 16, 1024);
-                  umma(dcol + (uint32_t)part * 128u, a, bd, id_mn, 1);
-                }
-              }
-            }
-            if (grp == 0)
-              asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                  smem_u32(&bar_lo[t])));
-          }
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(&bar_mma[t])));
-        }
-        mbar_arrive(&bar_full[t]);
-      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_ready[t]);
     }
-    // drain: the last item's MMAs must complete before the tiles and tensor memory go away
-    if (tid == 0 && n_mine > 0 && !*(volatile int *)&s_abort)
-      mbar_wait(&bar_mma[(n_mine - 1) & 1], (uint32_t)(((n_mine - 1) >> 1) & 1), op.err, &s_abort);
-  } else {
+  } else if (warp < kMmaWarp) {
     // ------------------------------------------------------------ epilogue
     const int ew = warp - kProducers / 32;          // 0..3: TMEM lane quadrant
     const int b = 32 * ew + lane;                   // TMEM lane = column b of w_n
@@ -328,7 +296,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       asm volatile("tcgen05.fence::after_thread_sync;");
       // out = alpha * (-i C); the system-bath kernel adds y and the rest next
       if (tid == kProducers) P.max_out[item] = 0u;
-      const float sc = P.alpha * op.inv_sh / s_scale[t];
+      const float sc = P.alpha * op.inv_sh / item_scale(P.max_in[item]);
       float2 *ob = P.out + item * dd;
       const uint32_t tcol = tmem + lane_field + (uint32_t)t * 256u;
       for (int a0 = 0; a0 < d; a0 += 16) {
@@ -349,6 +317,57 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar_epi[t]);
     }
+  } else {
+    // ------------------------------------------------------------ MMA issue
+    if (lane == 0) {
+      const uint32_t zz[2] = {smem_u32(ZZ1), smem_u32(ZZ2)};
+      const uint32_t hh = smem_u32(HT);
+      const uint32_t id_neg = idesc(128, 256, 0, 0, 1);
+      const uint32_t id_mn = idesc(128, 128, 1, 0, 0);
+      const int nh = op.n_hpieces;
+      for (int64_t k = 0; k < n_mine; ++k) {
+        const int t = (int)(k & 1);
+        // the tiles of item k are written; its accumulator buffer is free once
+        // the epilogue of item k - 2 released it
+        bool ok = mbar_wait(&bar_ready[t], (uint32_t)((k >> 1) & 1), op.err, &s_abort);
+        ok = ok && (k < 2 || mbar_wait(&bar_epi[t], (uint32_t)(((k - 2) >> 1) & 1), op.err, &s_abort));
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        // products kept by the split: H1 Z2 first (it frees the lo tiles), then
+        // H1 Z1 + H2 Z1 (+ H3 Z1) with the hi tiles
+        const uint32_t dcol = tmem + (uint32_t)t * 256u;
+        for (int grp = 0; grp < 2; ++grp) {
+          const int zk = grp == 0 ? 1 : 0;                 // Z piece of this group
+          const int j_hi = grp == 0 ? 1 : nh;               // H pieces of this group
+          for (int j = 0; j < j_hi; ++j) {
+            const uint32_t ha = hh + (uint32_t)j * kHTile, zb = zz[zk];
+            for (int kk = 0; kk < 8; ++kk) {
+              const uint64_t a = sdesc(ha + (kk >> 2) * 16384u + (kk & 3) * 32u, 16, 1024);
+              const uint64_t bd = sdesc(zb + (kk >> 2) * (kZZ / 2) + (kk & 3) * 32u, 16, 1024);
+              umma(dcol, a, bd, id_neg, (grp | j | kk) ? 1u : 0u);
+            }
+            for (int part = 0; part < 2; ++part) {
+              const uint32_t za = zz[zk] + (uint32_t)part * 16384u;
+              for (int kk = 0; kk < 8; ++kk) {
+                const uint64_t a = sdesc(za + (uint32_t)kk * 2048u, kZZ / 2, 1024);
+                const uint64_t bd = sdesc(ha + (kk >> 2) * 16384u + (kk & 3) * 32u, 16, 1024);
+                umma(dcol + (uint32_t)part * 128u, a, bd, id_mn, 1);
+              }
+            }
+          }
+          if (grp == 0)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&bar_lo[t])));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_u32(&bar_mma[t])));
+        mbar_arrive(&bar_full[t]);
+      }
+      // drain: the last item's MMAs must complete before the tiles and tensor memory go away
+      if (n_mine > 0 && !*(volatile int *)&s_abort)
+        mbar_wait(&bar_mma[(n_mine - 1) & 1], (uint32_t)(((n_mine - 1) >> 1) & 1), op.err, &s_abort);
+    }
+    __syncwarp();
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
