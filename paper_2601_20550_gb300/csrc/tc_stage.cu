@@ -229,27 +229,33 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       const float2 *wn = P.w + item * dd;
       // warm L2 with the next item's w_n while this one is converted (one bulk prefetch)
       if (k + 1 < n_mine && tid == 0) l2_prefetch_bulk(P.w + (item + gridDim.x) * dd, dd * 8);
-      // The lo tiles are free once the previous item's first MMA group (the
-      // products with Z2) has completed; every producer reaches the barrier, then
-      // all read the abort flag (uniform exit).
-      if (k >= 1) mbar_wait(&bar_lo[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort);
-      producer_sync();
-      if (*(volatile int *)&s_abort) break;
-      // power-of-two scale from the item's largest component (kept by the previous stage)
-      const float scale = item_scale(P.max_in[item]);
-      // scale and split into FP16 hi + lo; lo goes to the tiles now, hi is kept in
-      // registers until the previous item's remaining MMAs (with Z1) are done
-      __half2 hre[2 * kProdRows], him[2 * kProdRows];
-#pragma unroll
-      for (int bt = 0; bt < 2; ++bt) {
+      // The first batch of w_n is loaded before the wait, so its latency overlaps
+      // the previous item's first MMA group.
+      float2 v[2 * kProdRows];
+      auto load_batch = [&](int bt) {
         const int ab = r0 + 6 * kProdRows * bt;
-        float2 v[2 * kProdRows];
 #pragma unroll
         for (int i = 0; i < kProdRows; ++i) {
           const int a = min(ab + 6 * i, d - 1);
           v[2 * i] = active ? wn[(int64_t)a * d + c] : make_float2(0.f, 0.f);
           v[2 * i + 1] = (active && c + 1 < d) ? wn[(int64_t)a * d + c + 1] : make_float2(0.f, 0.f);
         }
+      };
+      load_batch(0);
+      // power-of-two scale from the item's largest component (kept by the previous stage)
+      const float scale = item_scale(P.max_in[item]);
+      // The lo tiles are free once the previous item's first MMA group (the
+      // products with Z2) has completed; every producer reaches the barrier, then
+      // all read the abort flag (uniform exit).
+      if (k >= 1) mbar_wait(&bar_lo[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort);
+      producer_sync();
+      if (*(volatile int *)&s_abort) break;
+      // scale and split into FP16 hi + lo; lo goes to the tiles now, hi is kept in
+      // registers until the previous item's remaining MMAs (with Z1) are done
+      __half2 hre[2 * kProdRows], him[2 * kProdRows];
+#pragma unroll
+      for (int bt = 0; bt < 2; ++bt) {
+        if (bt == 1) load_batch(1);
 #pragma unroll
         for (int i = 0; i < kProdRows; ++i) {
           const int g = kProdRows * bt + i;                  // row a = r0 + 6 g
