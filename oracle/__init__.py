@@ -17,6 +17,8 @@ heom  : right-hand side of Eq. HEOM_DB, classic RK4, equilibration, dipole
         kicks, traces, the 2D procedure and the 2D Fourier transforms
         (Sec. II.C; Eqs. R1, RFTIRI, echo, virtual-echo, 2D-rephasing,
         2D-nonrephasing, correlation-spectrum).
+adjoint : the squared misfit of S_C against a reference spectrum and its gradient
+        with respect to twelve model parameters, by central differences.
 
 Parity status: every function is pinned by a test in tests/test_oracle_*.py
 against closed forms, invariants, special cases or brute force; see the module
