@@ -192,6 +192,31 @@ heom_status heom_response_2d(heom_hier *h, const heom_state *rho_eq, const heom_
                              double *R_I, double *R_II, double *S_C);
 
 /*
+ * Gradient of the 2D-spectrum misfit
+ *   loss = sum_{t2, Omega1, Omega3} (S_C - S_ref)^2
+ * (S_C as in heom_response_2d, Eq. correlation-spectrum) with respect to twelve
+ * parameters of the model description:
+ *   dtheta[0..2]   anharmonicity of mode s (morse_D_cm of a Morse mode, g3_cm of a
+ *                  cubic one), dtheta[3..5] g_s2t_cm of pair p (pairs in model order),
+ *   dtheta[6..8]   V_SL of mode s, dtheta[9..11] gamma_cm of mode s (zeta_cm fixed);
+ * entries for modes or pairs the model lacks are 0.  S_ref is host
+ * [n_t2][n1][n3]; *loss and dtheta[12] are written.
+ * Method: reverse mode through everything the FP64 path computes -- the
+ * equilibration from |0><0| (rho_eq must come from heom_equilibrate; its step
+ * count and dt are replayed), the t1 trunk, both pathways' kicks, the t2 and t3
+ * propagation (Sec. II.C) and the Fourier sums -- with the RK4 steps reversed
+ * stage by stage (the adjoint right-hand side has the structure of Eq. HEOM_DB
+ * with H -> -H and the coupling lists transposed) and the states recomputed from
+ * checkpoints every ckpt_every steps.  The model matrices' derivatives with
+ * respect to each parameter are taken by fourth-order central differences of the
+ * host model build (relative step 1e-3) and contracted with the device-accumulated
+ * matrix gradients.  Requires a hierarchy built with HEOM_FP64 (HEOM_EINVAL otherwise);
+ * device memory is taken in chunks of t1 rows (HEOM_ENOMEM if one row does not fit).
+ */
+heom_status heom_response_2d_grad(heom_hier *h, const heom_state *rho_eq, const heom_grid *g,
+                                  const double *S_ref, int ckpt_every, double *loss, double *dtheta);
+
+/*
  * Several parameter sets (hierarchies of any basis size, each with its own
  * single-branch FP64 equilibrium) on one grid: outputs [n_sets][n_t2][n1][n3]
  * with the layouts of heom_response_2d (any output may be NULL).  Sets run one

@@ -5,6 +5,7 @@ include/heom2dvs.h; all arithmetic of the method runs in the library's CUDA
 kernels.  The library is loaded from this package directory and its absence is
 an error: there is no CPU fallback.
 """
+import copy
 import ctypes as ct
 import os
 
@@ -84,6 +85,7 @@ def lib():
         "heom_propagate_dev": [_P, _P, _P, _P, ct.c_int, ct.c_int, ct.c_double, ct.c_int64, _P],
         "heom_response_2d_rows": [_P, _P, ct.POINTER(heom_grid), ct.c_int, ct.c_int, _D, _D],
         "heom_response_2d_batched": [ct.POINTER(_P), ct.POINTER(_P), ct.c_int, ct.POINTER(heom_grid), _D, _D, _D],
+        "heom_response_2d_grad": [_P, _P, ct.POINTER(heom_grid), _D, ct.c_int, _D, _D],
         "heom_state_broadcast": [_P, _P],
         "heom_spectrum_2d": [_D, _D, ct.c_int, ct.c_int, ct.c_int, ct.c_double, _D],
         "heom_trace_dev": [_P, _P, ct.c_int, ct.c_int, ct.c_int, _P, _P],
@@ -273,6 +275,53 @@ def heom_response_2d_batched(hiers, eqs, grid):
     _check(lib().heom_response_2d_batched(harr, earr, n, ct.byref(g), RI.ctypes.data_as(_D),
                                           RII.ctypes.data_as(_D), SC.ctypes.data_as(_D)))
     return RI, RII, SC
+
+
+N_THETA = 12
+
+
+def _theta_slot(model, i):
+    """(dict, key) of gradient parameter i in a model description, or None."""
+    grp, k = divmod(i, 3)
+    if grp == 1:
+        return (model["pairs"][k], "g_s2t_cm") if k < len(model["pairs"]) else None
+    if k >= len(model["modes"]):
+        return None
+    md = model["modes"][k]
+    if grp == 0:
+        return (md, "morse_D_cm") if md["potential"] == "morse" else (md, "g3_cm")
+    return (md, "V_SL") if grp == 2 else (md, "gamma_cm")
+
+
+def theta_of(model):
+    """The twelve gradient parameters of a model description (dtheta order of heom_response_2d_grad)."""
+    th = np.zeros(N_THETA)
+    for i in range(N_THETA):
+        s = _theta_slot(model, i)
+        if s is not None:
+            th[i] = s[0][s[1]]
+    return th
+
+
+def with_theta(model, theta):
+    """Copy of a model description with the twelve parameters replaced."""
+    out = copy.deepcopy(model)
+    for i in range(N_THETA):
+        s = _theta_slot(out, i)
+        if s is not None:
+            s[0][s[1]] = float(theta[i])
+    return out
+
+
+def heom_response_2d_grad(h, rho_eq, grid, S_ref, ckpt_every=64):
+    """(loss, dtheta[12]) of the squared misfit of S_C against S_ref [n_t2][n1][n3]."""
+    g = marshal_grid(grid)
+    S = np.ascontiguousarray(S_ref, dtype=np.float64).reshape(len(grid["t2_fs"]), grid["n1"], grid["n3"])
+    loss = np.zeros(1)
+    dth = np.zeros(12)
+    _check(lib().heom_response_2d_grad(h.h, rho_eq.h, ct.byref(g), S.ctypes.data_as(_D), int(ckpt_every),
+                                       loss.ctypes.data_as(_D), dth.ctypes.data_as(_D)))
+    return float(loss[0]), dth
 
 
 def heom_response_2d_rows(h, rho_eq, grid, j0, j1):
