@@ -38,6 +38,7 @@ WORKLOADS = {
     "c2-fp64": ("c2", 0, 2),
     "c3-fp64": ("c3", 0, 2),
     "c1-fp64": ("c1", 0, 64),
+    "c4-grad": ("c4", 0, 0),       # adjoint gradient of the spectrum misfit (own JSON line)
 }
 PREC_NAME = {0: "f64", 1: "f32", 2: "fp16x2-tc-f32acc"}
 
@@ -209,6 +210,46 @@ def run_reference(args, cfg, rank, world):
 
 
 # ---------------------------------------------------------------------------
+def run_grad(args, local):
+    """One heom_response_2d_grad call on the c4 model (FP64), timed end to end.
+
+    S_ref is the library's own S_C at theta_ref = theta (1 + 0.05 U(-1, 1)), seed 2604;
+    the grid is the c4 grid cut to --grad-n x --grad-n (t1 x t3).  value = ADO-updates of
+    the forward procedure (equilibration, trunk, both pathways' t3 scans) per second of
+    the whole gradient call (forward, recomputation, reverse pass, host chain rule).
+    """
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2601_20550_gb300 import heom as H
+    model, grid = W.config("c4")
+    grid["n1"] = grid["n3"] = args.grad_n
+    th = H.theta_of(model)
+    rng = np.random.default_rng(2604)
+    m_ref = H.with_theta(model, th * (1 + 0.05 * rng.uniform(-1, 1, th.size)))
+    h_ref = H.heom_build_hierarchy(m_ref, 0)
+    eq_ref = H.heom_equilibrate(h_ref, grid["dt_fs"], grid["t_eq_fs"], 0.0)
+    S_ref = H.heom_response_2d(h_ref, eq_ref, grid)[2]
+    h = H.heom_build_hierarchy(model, 0)
+    eq = H.heom_equilibrate(h, grid["dt_fs"], grid["t_eq_fs"], 0.0)
+    nado, m, n1, n3 = h.n_ado, grid["steps_per_sample"], grid["n1"], grid["n3"]
+    fwd = (round(grid["t_eq_fs"] / grid["dt_fs"]) + (n1 - 1) * m + 2 * n1 * (n3 - 1) * m) * nado
+    torch.cuda.synchronize()
+    n_launch0 = H.heom_launch_count()
+    t0 = time.perf_counter()
+    loss, g = H.heom_response_2d_grad(h, eq, grid, S_ref, 64)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    launches = H.heom_launch_count() - n_launch0
+    print(json.dumps({
+        "metric": "c4 misfit gradient, forward-equivalent HEOM ADO-updates/s", "value": fwd / el,
+        "unit": "ADO-updates/s", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True,
+        "dtype": "f64", "data": "synthetic (seeded water-like MAB model; S_ref from seeded theta_ref)",
+        "config": {"workload": "c4: 3-mode MAB, d=%d, %d ADOs (L=4), %dx%d t1xt3, t2=0, dt=0.5 fs, m=8, "
+                               "12 parameters, checkpoints every 64 steps" % (h.d, nado, n1, n3)},
+        "seconds_per_gradient": el, "forward_ado_updates": fwd, "loss": loss,
+        "dtheta": list(map(float, g)), "gpu_launches": int(launches)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -221,6 +262,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--grad-n", type=int, default=16, help="t1 and t3 samples of the c4-grad workload")
     ap.add_argument("--branches", type=int, default=0,
                     help="override the batch (profiling runs only; default 2*n1)")
     args = ap.parse_args()
@@ -231,6 +273,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, cfg, rank, world)
+        return
+    if args.workload == "c4-grad":
+        if rank == 0:
+            run_grad(args, local)
         return
 
     import torch

@@ -192,6 +192,17 @@ heom_status heom_response_2d(heom_hier *h, const heom_state *rho_eq, const heom_
                              double *R_I, double *R_II, double *S_C);
 
 /*
+ * Launch shapes chosen by the library's autotuner (no counterpart in the paper:
+ * a tuning aid).  The first RK4 propagation of a given size on the FP64
+ * (kind 0) or FP32 coupling-basis (kind 1) path times nine launch shapes of its
+ * stage kernel (64/128/256 threads x 4/16/64 blocks per SM) on the real operands
+ * and keeps the fastest; results do not depend on the shape.  Returns the number
+ * of tuned (kind, elements) entries of h and copies up to cap of them (any
+ * pointer may be NULL).
+ */
+int heom_get_tuning(const heom_hier *h, int cap, int *kind, int64_t *elements, int *block, int *grid);
+
+/*
  * Gradient of the 2D-spectrum misfit
  *   loss = sum_{t2, Omega1, Omega3} (S_C - S_ref)^2
  * (S_C as in heom_response_2d, Eq. correlation-spectrum) with respect to twelve
@@ -219,8 +230,12 @@ heom_status heom_response_2d_grad(heom_hier *h, const heom_state *rho_eq, const 
 /*
  * Several parameter sets (hierarchies of any basis size, each with its own
  * single-branch FP64 equilibrium) on one grid: outputs [n_sets][n_t2][n1][n3]
- * with the layouts of heom_response_2d (any output may be NULL).  Sets run one
- * after the other, each with all its branches batched.
+ * with the layouts of heom_response_2d (any output may be NULL).  When every
+ * set is an HEOM_FP64 hierarchy, the sets advance together: each RK4 stage of
+ * all sets and all their branches is one kernel launch (per-set models and
+ * state pointers in a descriptor table), and each t3 scan is one CUDA-graph
+ * replay; results equal those of heom_response_2d per set.  Otherwise the sets
+ * run one after the other, each with all its branches batched.
  */
 heom_status heom_response_2d_batched(heom_hier *const *hs, const heom_state *const *eqs, int n_sets,
                                      const heom_grid *g, double *R_I, double *R_II, double *S_C);

@@ -9,9 +9,12 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <future>
 #include <memory>
 #include <stdexcept>
 #include <string>
+#include <map>
+#include <utility>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -116,6 +119,8 @@ struct heom_hier {
   std::vector<heom_mode> desc_modes;
   std::vector<heom_pair> desc_pairs;
   // adjoint RHS tables (built on the first gradient call)
+  // launch shapes picked by the autotuner: (kernel kind, elements) -> (block, grid)
+  std::map<std::pair<int, int64_t>, std::pair<int, int>> tuned;
   bool adj_ready = false;
   DevModel<double> dm_adj{};
   int *adj_ado = nullptr, *adj_entry_exp = nullptr;
@@ -197,6 +202,58 @@ static void stability_check(heom_hier *h, double dt) {
                                    std::to_string(dt * maxdecay) + ")"};
 }
 
+// Launch-shape autotuner for the grid-stride stage kernels.  The first launch of
+// a kernel kind at a given size times every candidate (block of 64, 128 or 256
+// threads; 4, 16 or 64 blocks per SM, capped at one element per thread) on the
+// real operands -- three timed launches each after one untimed -- and keeps the
+// fastest for this hierarchy.  Candidate launches repeat the caller's first
+// stage, whose output is scratch that the step overwrites next, so tuning
+// changes no result.  Inside a stream capture, or when timing fails, the
+// default shape (256 threads, grid_for) is used and nothing is cached.
+enum TuneKind { kTuneStage64 = 0, kTuneStageVb = 1 };
+
+static std::pair<int, int> tuned_shape(heom_hier *h, int kind, int64_t total, cudaStream_t st,
+                                       const std::function<void(int, int)> &launch) {
+  const std::pair<int, int> dflt(256, grid_for(total));
+  auto it = h->tuned.find({kind, total});
+  if (it != h->tuned.end()) return it->second;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return dflt;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    cudaGetLastError();
+    return dflt;
+  }
+  std::pair<int, int> best = dflt;
+  float best_ms = 1e30f;
+  bool ok = true;
+  for (int block : {64, 128, 256})
+    for (int per_sm : {4, 16, 64}) {
+      const int64_t need = (total + block - 1) / block;
+      const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(need, 152LL * per_sm * 256 / block));
+      launch(block, grid);
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < 3; ++r) launch(block, grid);
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        ok = false;
+        break;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = {block, grid};
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  LAUNCH_CHECK();
+  if (!ok) return dflt;
+  h->tuned[{kind, total}] = best;
+  return best;
+}
+
 // One RK4 step on branches [y] with scratch wa, wb, Horner form:
 //   wa = y + dt/4 L(y); wb = y + dt/3 L(wa); wa = y + dt/2 L(wb); y = y + dt L(wa)
 template <typename R>
@@ -212,24 +269,32 @@ static void rk4_steps(heom_hier *h, typename CxT<R>::type *y, typename CxT<R>::t
       if (!tc_supported(h->tc)) throw Fail{HEOM_EINVAL, "tensor-core path not prepared for this hierarchy"};
       tc_rk4_steps(h->tc, fy, fa, fb, branches, dt, nsteps, st);
     } else {
-      const int grid = grid_for(total);
+      const auto sh = tuned_shape(h, kTuneStageVb, total, st, [&](int block, int grid) {
+        stage_kernel_vb<<<grid, block, 0, st>>>(fy, fy, fa, (float)(dt / 4), h->vb, total);
+        count_launch(1);
+      });
+      const int grid = sh.second, block = sh.first;
       for (int64_t s = 0; s < nsteps; ++s) {
-        stage_kernel_vb<<<grid, 256, 0, st>>>(fy, fy, fa, (float)(dt / 4), h->vb, total);
-        stage_kernel_vb<<<grid, 256, 0, st>>>(fa, fy, fb, (float)(dt / 3), h->vb, total);
-        stage_kernel_vb<<<grid, 256, 0, st>>>(fb, fy, fa, (float)(dt / 2), h->vb, total);
-        stage_kernel_vb<<<grid, 256, 0, st>>>(fa, fy, fy, (float)dt, h->vb, total);
+        stage_kernel_vb<<<grid, block, 0, st>>>(fy, fy, fa, (float)(dt / 4), h->vb, total);
+        stage_kernel_vb<<<grid, block, 0, st>>>(fa, fy, fb, (float)(dt / 3), h->vb, total);
+        stage_kernel_vb<<<grid, block, 0, st>>>(fb, fy, fa, (float)(dt / 2), h->vb, total);
+        stage_kernel_vb<<<grid, block, 0, st>>>(fa, fy, fy, (float)dt, h->vb, total);
         count_launch(4);
       }
     }
     LAUNCH_CHECK();
     return;
   }
-  const int grid = grid_for(total);
+  const auto sh = tuned_shape(h, kTuneStage64, total, st, [&](int block, int grid) {
+    stage_kernel<R><<<grid, block, 0, st>>>(y, y, wa, (R)(dt / 4), dm, total);
+    count_launch(1);
+  });
+  const int grid = sh.second, block = sh.first;
   for (int64_t s = 0; s < nsteps; ++s) {
-    stage_kernel<R><<<grid, 256, 0, st>>>(y, y, wa, (R)(dt / 4), dm, total);
-    stage_kernel<R><<<grid, 256, 0, st>>>(wa, y, wb, (R)(dt / 3), dm, total);
-    stage_kernel<R><<<grid, 256, 0, st>>>(wb, y, wa, (R)(dt / 2), dm, total);
-    stage_kernel<R><<<grid, 256, 0, st>>>(wa, y, y, (R)dt, dm, total);
+    stage_kernel<R><<<grid, block, 0, st>>>(y, y, wa, (R)(dt / 4), dm, total);
+    stage_kernel<R><<<grid, block, 0, st>>>(wa, y, wb, (R)(dt / 3), dm, total);
+    stage_kernel<R><<<grid, block, 0, st>>>(wb, y, wa, (R)(dt / 2), dm, total);
+    stage_kernel<R><<<grid, block, 0, st>>>(wa, y, y, (R)dt, dm, total);
     count_launch(4);
   }
   LAUNCH_CHECK();
@@ -473,6 +538,164 @@ static void ensure_device(heom_hier *h) {
   h->vb = vb;
   if (M.precision == HEOM_TC) tc_build(h->tc, M, h->vb, h->allocs);
   h->on_device = true;
+}
+
+}  // namespace heom
+
+namespace heom {
+
+// Several FP64 parameter sets (hierarchies of any basis size) on one grid, with
+// every RK4 stage of all sets in one launch of multi_stage_kernel.  The branch
+// schedule is that of response_2d_rows_impl (one t1 trunk per set, both
+// pathways from it, t2 forks in ascending order, the t3 scan captured once into
+// a CUDA graph); kicks and traces stay per set (they are cheap).  Rdev[k] gets
+// set k's R in the layout [n_t2][2][n1][n3].
+struct MultiSet {
+  heom_hier *h;
+  const heom_state *eq;
+  int64_t per;                                     // n_ado d^2
+  std::unique_ptr<DeviceBuffer> T, ta, tb, P[4];   // trunk and its scratch; branch sets
+};
+
+// Descriptor arrays (device) for the four Horner stages of one RK4 step on the
+// buffers (y, wa, wb) of every set.
+struct MultiStep {
+  DeviceBuffer desc[4];
+  int64_t grand = 0;
+};
+
+static void multi_step_setup(std::vector<MultiSet> &S, MultiStep &ms, int which_y, int which_a, int which_b,
+                             int branches, cudaStream_t st) {
+  const int n = (int)S.size();
+  std::vector<SetStage<double>> d4[4];
+  int64_t begin = 0;
+  for (int k = 0; k < n; ++k) {
+    auto buf = [&](int w) -> double2 * {
+      if (w == -1) return (double2 *)S[k].T->p;
+      if (w == -2) return (double2 *)S[k].ta->p;
+      if (w == -3) return (double2 *)S[k].tb->p;
+      return (double2 *)S[k].P[w]->p;
+    };
+    double2 *y = buf(which_y), *wa = buf(which_a), *wb = buf(which_b);
+    const int64_t tot = (int64_t)branches * S[k].per;
+    const double2 *ws[4] = {y, wa, wb, wa};
+    double2 *outs[4] = {wa, wb, wa, y};
+    for (int q = 0; q < 4; ++q) {
+      SetStage<double> x{};
+      x.M = S[k].h->dm64;
+      x.w = ws[q];
+      x.y = y;
+      x.out = outs[q];
+      x.begin = begin;
+      x.total = tot;
+      d4[q].push_back(x);
+    }
+    begin += tot;
+  }
+  ms.grand = begin;
+  for (int q = 0; q < 4; ++q) {
+    ms.desc[q].alloc(sizeof(SetStage<double>) * n);
+    CUDA_TRY(cudaMemcpyAsync(ms.desc[q].p, d4[q].data(), sizeof(SetStage<double>) * n, cudaMemcpyHostToDevice, st));
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+static void multi_rk4(const MultiStep &ms, int n_sets, double dt, int64_t nsteps, cudaStream_t st) {
+  if (ms.grand == 0 || nsteps <= 0) return;
+  const double al[4] = {dt / 4, dt / 3, dt / 2, dt};
+  const int grid = grid_for(ms.grand);
+  for (int64_t s = 0; s < nsteps; ++s) {
+    for (int q = 0; q < 4; ++q)
+      multi_stage_kernel<double><<<grid, 256, 0, st>>>((const SetStage<double> *)ms.desc[q].p, n_sets, al[q],
+                                                       ms.grand);
+    count_launch(4);
+  }
+  LAUNCH_CHECK();
+}
+
+}  // namespace heom
+
+namespace heom {
+
+static void response_2d_multi(heom_hier *const *hs, const heom_state *const *eqs, int n_sets, const heom_grid *g,
+                              const std::vector<double2 *> &Rdev) {
+  cudaStream_t st = hs[0]->stream;
+  const int n1 = g->n1, n3 = g->n3, m = g->steps_per_sample, nt2 = g->n_t2;
+  const double dt = g->dt_fs;
+  std::vector<int> order(nt2);
+  std::vector<int64_t> n2(nt2);
+  for (int i = 0; i < nt2; ++i) {
+    order[i] = i;
+    const double r = g->t2_fs[i] / dt;
+    n2[i] = (int64_t)std::llround(r);
+    if (g->t2_fs[i] < 0 || std::fabs(r - n2[i]) > 1e-6) throw Fail{HEOM_EINVAL, "t2 must be a non-negative multiple of dt"};
+  }
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return n2[a] < n2[b]; });
+  std::vector<MultiSet> S(n_sets);
+  int64_t sum_per = 0;
+  for (int k = 0; k < n_sets; ++k) {
+    const Model &M = hs[k]->M;
+    S[k].h = hs[k];
+    S[k].eq = eqs[k];
+    S[k].per = (int64_t)M.n_ado * M.d * M.d;
+    sum_per += S[k].per;
+    S[k].T.reset(new DeviceBuffer(S[k].per * 16));
+    S[k].ta.reset(new DeviceBuffer(S[k].per * 16));
+    S[k].tb.reset(new DeviceBuffer(S[k].per * 16));
+  }
+  // t1 rows per chunk: both pathways of J rows, 3 or 4 branch sets per parameter set
+  const int nbuf = nt2 > 1 ? 4 : 3;
+  size_t free_b = 0, total_b = 0;
+  CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  const double budget = 0.85 * (double)free_b;
+  int J = n1;
+  while (J > 1 && (double)nbuf * 2 * J * sum_per * 16 > budget) J = (J + 1) / 2;
+  if ((double)nbuf * 2 * J * sum_per * 16 > budget) throw Fail{HEOM_ENOMEM, "states do not fit in device memory"};
+  for (int k = 0; k < n_sets; ++k)
+    for (int q = 0; q < 4; ++q)
+      S[k].P[q].reset(new DeviceBuffer(q < nbuf ? (size_t)2 * J * S[k].per * 16 : 16));
+  MultiStep trunk;
+  multi_step_setup(S, trunk, -1, -2, -3, 1, st);
+  for (int j0 = 0; j0 < n1; j0 += J) {
+    const int nj = std::min(J, n1 - j0), B = 2 * nj;
+    MultiStep fork, scan;
+    multi_step_setup(S, fork, 0, 1, 2, B, st);                       // y = BR, scratch Y, WA
+    multi_step_setup(S, scan, 1, 2, nbuf == 4 ? 3 : 0, B, st);       // y = Y, scratch WA, WB
+    for (int k = 0; k < n_sets; ++k)
+      kick_into<double>(S[k].h, (const double2 *)S[k].eq->buf.p, (double2 *)S[k].T->p, 1, 2, st);
+    multi_rk4(trunk, n_sets, dt, (int64_t)j0 * m, st);
+    for (int j = 0; j < nj; ++j) {
+      if (j > 0) multi_rk4(trunk, n_sets, dt, m, st);
+      for (int k = 0; k < n_sets; ++k) {
+        const int64_t per = S[k].per;
+        double2 *br = (double2 *)S[k].P[0]->p;
+        kick2_pair_kernel<double><<<grid_for(per), 256, 0, st>>>((const double2 *)S[k].T->p, br + (int64_t)j * per,
+                                                                br + (int64_t)(nj + j) * per, S[k].h->mup64,
+                                                                S[k].h->mum64, S[k].h->M.d, per);
+        count_launch(1);
+        LAUNCH_CHECK();
+      }
+    }
+    int64_t t_now = 0;
+    for (int oi = 0; oi < nt2; ++oi) {
+      const int it = order[oi];
+      multi_rk4(fork, n_sets, dt, n2[it] - t_now, st);
+      t_now = n2[it];
+      for (int k = 0; k < n_sets; ++k)
+        kick_into<double>(S[k].h, (const double2 *)S[k].P[0]->p, (double2 *)S[k].P[1]->p, B, 1, st);
+      GraphCapture cap(st);
+      for (int kk = 0; kk < n3; ++kk) {
+        if (kk > 0) multi_rk4(scan, n_sets, dt, m, st);
+        for (int k = 0; k < n_sets; ++k)
+          for (int pw = 0; pw < 2; ++pw) {
+            double2 *base = Rdev[k] + (int64_t)it * 2 * n1 * n3 + (int64_t)pw * n1 * n3 + (int64_t)j0 * n3 + kk;
+            trace_into<double>(S[k].h, (const double2 *)S[k].P[1]->p + (int64_t)pw * nj * S[k].per, nj, 3, base, n3, st);
+          }
+      }
+      cap.replay();
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
 }
 
 }  // namespace heom
@@ -791,12 +1014,56 @@ heom_status heom_response_2d_batched(heom_hier *const *hs, const heom_state *con
                                      const heom_grid *g, double *R_I, double *R_II, double *S_C) {
   if (!hs || !eqs || !g || n_sets < 1) return fail(HEOM_EINVAL, "bad batched arguments");
   const size_t blk = (size_t)g->n_t2 * g->n1 * g->n3;
+  bool one_launch = n_sets > 1;
   for (int i = 0; i < n_sets; ++i) {
-    heom_status st = heom_response_2d(hs[i], eqs[i], g, R_I ? R_I + i * blk * 2 : nullptr,
-                                      R_II ? R_II + i * blk * 2 : nullptr, S_C ? S_C + i * blk : nullptr);
-    if (st != HEOM_OK) return st;
+    heom_status a = check_response_args(hs[i], eqs[i], g);
+    if (a != HEOM_OK) return a;
+    one_launch = one_launch && hs[i]->M.precision == HEOM_FP64;
   }
-  return HEOM_OK;
+  if (!one_launch) {
+    for (int i = 0; i < n_sets; ++i) {
+      heom_status st = heom_response_2d(hs[i], eqs[i], g, R_I ? R_I + i * blk * 2 : nullptr,
+                                        R_II ? R_II + i * blk * 2 : nullptr, S_C ? S_C + i * blk : nullptr);
+      if (st != HEOM_OK) return st;
+    }
+    return HEOM_OK;
+  }
+  return guarded([&]() -> heom_status {
+    for (int i = 0; i < n_sets; ++i) {
+      ensure_device(hs[i]);
+      stability_check(hs[i], g->dt_fs);
+    }
+    cudaStream_t st = hs[0]->stream;
+    const int n1 = g->n1, n3 = g->n3, nt2 = g->n_t2;
+    const size_t one = (size_t)n1 * n3;
+    DeviceBuffer Rall((size_t)n_sets * nt2 * 2 * one * 16), SCall((size_t)n_sets * blk * 8);
+    CUDA_TRY(cudaMemsetAsync(Rall.p, 0, Rall.bytes, st));
+    std::vector<double2 *> Rdev(n_sets);
+    for (int i = 0; i < n_sets; ++i) Rdev[i] = (double2 *)Rall.p + (size_t)i * nt2 * 2 * one;
+    response_2d_multi(hs, eqs, n_sets, g, Rdev);
+    const double dtau = g->dt_fs * g->steps_per_sample;
+    for (int i = 0; i < n_sets; ++i)
+      for (int it = 0; it < nt2; ++it) {
+        double2 *RI = Rdev[i] + (int64_t)it * 2 * one;
+        dft2d_sc_kernel<<<(unsigned)((one + 255) / 256), 256, 0, st>>>(RI, RI + one, n1, n3, dtau,
+                                                                       (double *)SCall.p + (size_t)i * blk + it * one);
+        count_launch(1);
+        LAUNCH_CHECK();
+      }
+    std::vector<double> Rh(Rall.bytes / 8);
+    CUDA_TRY(cudaMemcpyAsync(Rh.data(), Rall.p, Rall.bytes, cudaMemcpyDeviceToHost, st));
+    if (S_C) CUDA_TRY(cudaMemcpyAsync(S_C, SCall.p, SCall.bytes, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int i = 0; i < n_sets; ++i)
+      for (int it = 0; it < nt2; ++it) {
+        const double *src = Rh.data() + ((size_t)i * nt2 * 2 + (size_t)it * 2) * one * 2;
+        if (R_I) std::memcpy(R_I + ((size_t)i * blk + it * one) * 2, src, one * 16);
+        if (R_II) std::memcpy(R_II + ((size_t)i * blk + it * one) * 2, src + one * 2, one * 16);
+      }
+    for (double v : Rh)
+      if (!std::isfinite(v)) throw Fail{HEOM_ENONFINITE, "response is not finite"};
+    return HEOM_OK;
+  });
 }
 
 heom_status heom_response_2d_rows(heom_hier *h, const heom_state *rho_eq, const heom_grid *g, int j0, int j1,
@@ -1217,6 +1484,39 @@ extern "C" heom_status heom_response_2d_grad(heom_hier *h, const heom_state *rho
     ensure_adjoint(h);
     const Model &M = h->M;
     cudaStream_t st = h->stream;
+    // d(model matrices)/d theta by fourth-order central differences of the host model
+    // build, (8 (M(+h) - M(-h)) - (M(+2h) - M(-2h))) / (12 h), relative step 1e-3: the
+    // 4 x 12 builds run on host threads while the GPU does the reverse pass
+    struct Build {
+      int i;
+      double step;
+      std::future<Model> p1, m1, p2, m2;
+    };
+    auto model_at = [h](int i, double delta) {
+      heom_model md = h->desc;
+      std::vector<heom_mode> mds = h->desc_modes;
+      std::vector<heom_pair> ps = h->desc_pairs;
+      *theta_slot(md, mds, ps, i) += delta;
+      md.modes = mds.data();
+      md.pairs = ps.empty() ? nullptr : ps.data();
+      return build_model(md);
+    };
+    std::vector<Build> builds;
+    for (int i = 0; i < 12; ++i) {
+      heom_model md0 = h->desc;
+      std::vector<heom_mode> m0 = h->desc_modes;
+      std::vector<heom_pair> p0 = h->desc_pairs;
+      double *v0 = theta_slot(md0, m0, p0, i);
+      if (!v0) continue;
+      Build b;
+      b.i = i;
+      b.step = 1e-3 * std::max(std::fabs(*v0), 1.0);
+      b.p1 = std::async(std::launch::async, model_at, i, b.step);
+      b.m1 = std::async(std::launch::async, model_at, i, -b.step);
+      b.p2 = std::async(std::launch::async, model_at, i, 2 * b.step);
+      b.m2 = std::async(std::launch::async, model_at, i, -2 * b.step);
+      builds.push_back(std::move(b));
+    }
     const int d = M.d, n1 = g->n1, n3 = g->n3, m = g->steps_per_sample, nt2 = g->n_t2, Mck = ckpt_every;
     const double dt = g->dt_fs, dtau = dt * m;
     const int64_t per = (int64_t)M.n_ado * d * d, dd = (int64_t)d * d;
@@ -1378,28 +1678,11 @@ extern "C" heom_status heom_response_2d_grad(heom_hier *h, const heom_state *rho
     std::vector<double> G(c.L.total);
     CUDA_TRY(cudaMemcpyAsync(G.data(), Gd.p, Gd.bytes, cudaMemcpyDeviceToHost, st));
     CUDA_TRY(cudaStreamSynchronize(st));
-    // ---- chain rule to the twelve parameters: model matrices differentiated by
-    // central differences of the host model build
+    // ---- chain rule to the twelve parameters
     for (int i = 0; i < 12; ++i) dtheta[i] = 0.0;
-    // fourth-order central differences: dM = (8 (M(+h) - M(-h)) - (M(+2h) - M(-2h))) / (12 h)
-    auto model_at = [&](int i, double delta) {
-      heom_model md = h->desc;
-      std::vector<heom_mode> mds = h->desc_modes;
-      std::vector<heom_pair> ps = h->desc_pairs;
-      *theta_slot(md, mds, ps, i) += delta;
-      md.modes = mds.data();
-      md.pairs = ps.empty() ? nullptr : ps.data();
-      return build_model(md);
-    };
-    for (int i = 0; i < 12; ++i) {
-      heom_model md0 = h->desc;
-      std::vector<heom_mode> m0 = h->desc_modes;
-      std::vector<heom_pair> p0 = h->desc_pairs;
-      double *v0 = theta_slot(md0, m0, p0, i);
-      if (!v0) continue;
-      const double hs = 1e-3 * std::max(std::fabs(*v0), 1.0);
-      const Model P1 = model_at(i, hs), M1 = model_at(i, -hs), P2 = model_at(i, 2 * hs), M2 = model_at(i, -2 * hs);
-      const double inv = 1.0 / (12 * hs);
+    for (Build &b : builds) {
+      const Model P1 = b.p1.get(), M1 = b.m1.get(), P2 = b.p2.get(), M2 = b.m2.get();
+      const double inv = 1.0 / (12 * b.step);
       auto dv = [&](double p1, double m1, double p2, double m2) { return (8 * (p1 - m1) - (p2 - m2)) * inv; };
       double s = 0;
       for (int64_t k = 0; k < dd; ++k) {
@@ -1418,11 +1701,26 @@ extern "C" heom_status heom_response_2d_grad(heom_hier *h, const heom_state *rho
         s += G[c.L.im + j] * dv(P1.exp_im[j], M1.exp_im[j], P2.exp_im[j], M2.exp_im[j]);
         s += G[c.L.nu + j] * dv(P1.exp_nu[j], M1.exp_nu[j], P2.exp_nu[j], M2.exp_nu[j]);
       }
-      dtheta[i] = s;
+      dtheta[b.i] = s;
     }
     *loss = L2;
     for (int i = 0; i < 12; ++i)
       if (!std::isfinite(dtheta[i])) throw Fail{HEOM_ENONFINITE, "gradient is not finite"};
     return HEOM_OK;
   });
+}
+
+extern "C" int heom_get_tuning(const heom_hier *h, int cap, int *kind, int64_t *elements, int *block, int *grid) {
+  if (!h) return 0;
+  int k = 0;
+  for (const auto &e : h->tuned) {
+    if (k < cap) {
+      if (kind) kind[k] = e.first.first;
+      if (elements) elements[k] = e.first.second;
+      if (block) block[k] = e.second.first;
+      if (grid) grid[k] = e.second.second;
+    }
+    ++k;
+  }
+  return k;
 }

@@ -38,69 +38,99 @@ struct DevModel {
 // One thread per output element; out may alias y (each element is read and
 // written by the same thread) but not w.
 // ---------------------------------------------------------------------------
+// One element e of the fused stage (branch, ADO, row, column flattened).
+template <typename R>
+__device__ __forceinline__ void stage_element(const typename CxT<R>::type *__restrict__ w,
+                                              const typename CxT<R>::type *y, typename CxT<R>::type *out,
+                                              R alpha, const DevModel<R> &M, int64_t e) {
+  using C = typename CxT<R>::type;
+  const int d = M.d;
+  const int64_t dd = (int64_t)d * d;
+  const int64_t el = e % dd;
+  const int64_t bn = e / dd;
+  const int n = (int)(bn % M.n_ado);
+  const int64_t br = bn / M.n_ado;
+  const int a = (int)(el / d), b = (int)(el % d);
+  const C *wb = w + br * M.n_ado * dd;
+  const C *wn = wb + (int64_t)n * dd;
+  R re = 0, im = 0;
+  const R *Ha = M.H + (int64_t)a * d;
+  for (int c = 0; c < d; ++c) {
+    const R h1 = Ha[c];
+    const R h2 = M.H[(int64_t)c * d + b];
+    const C x = wn[(int64_t)c * d + b];
+    const C z = wn[(int64_t)a * d + c];
+    re += h1 * x.x - z.x * h2;
+    im += h1 * x.y - z.y * h2;
+  }
+  // -i [H, w]
+  R ore = im, oim = -re;
+  const R dec = (R)M.decay[n];
+  const C self = wn[el];
+  ore -= dec * self.x;
+  oim -= dec * self.y;
+  for (int s = 0; s < M.n_modes; ++s) {
+    const int o0 = M.nb_off[n * M.n_modes + s], o1 = M.nb_off[n * M.n_modes + s + 1];
+    if (o0 == o1) continue;
+    const int ns = M.dims[s], st = M.stride[s];
+    const int as = (a / st) % ns, bs = (b / st) % ns;
+    const int abase = a - as * st, bbase = b - bs * st;
+    const R *V = M.vloc + M.vloc_off[s];
+    for (int q = o0; q < o1; ++q) {
+      const C *wm = wb + (int64_t)M.nb_idx[q] * dd;
+      R lx = 0, ly = 0, rx = 0, ry = 0;
+      for (int k = 0; k < ns; ++k) {
+        const R vl = V[as * ns + k];
+        const C xl = wm[(int64_t)(abase + k * st) * d + b];
+        lx += vl * xl.x;
+        ly += vl * xl.y;
+        const R vr = V[k * ns + bs];
+        const C xr = wm[(int64_t)a * d + bbase + k * st];
+        rx += xr.x * vr;
+        ry += xr.y * vr;
+      }
+      const R cA = M.nb_cA[q], cB = M.nb_cB[q];
+      ore += cA * (ly - ry) + cB * (lx + rx);
+      oim += -cA * (lx - rx) + cB * (ly + ry);
+    }
+  }
+  const C yv = y[e];
+  C o;
+  o.x = yv.x + alpha * ore;
+  o.y = yv.y + alpha * oim;
+  out[e] = o;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) stage_kernel(const typename CxT<R>::type *__restrict__ w,
                                                     const typename CxT<R>::type *y,
                                                     typename CxT<R>::type *out, R alpha,
                                                     DevModel<R> M, int64_t total) {
-  using C = typename CxT<R>::type;
-  const int d = M.d;
-  const int64_t dd = (int64_t)d * d;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x)
+    stage_element<R>(w, y, out, alpha, M, e);
+}
+
+// The same stage for several hierarchies (parameter sets, any basis size) in one
+// launch: set k owns elements [begin_k, begin_k + total_k) of the flattened
+// index space and has its own model and state pointers.
+template <typename R>
+struct SetStage {
+  DevModel<R> M;
+  const typename CxT<R>::type *w, *y;
+  typename CxT<R>::type *out;
+  int64_t begin, total;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) multi_stage_kernel(const SetStage<R> *__restrict__ sets, int n_sets,
+                                                          R alpha, int64_t grand_total) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < grand_total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t el = e % dd;
-    const int64_t bn = e / dd;
-    const int n = (int)(bn % M.n_ado);
-    const int64_t br = bn / M.n_ado;
-    const int a = (int)(el / d), b = (int)(el % d);
-    const C *wb = w + br * M.n_ado * dd;
-    const C *wn = wb + (int64_t)n * dd;
-    R re = 0, im = 0;
-    const R *Ha = M.H + (int64_t)a * d;
-    for (int c = 0; c < d; ++c) {
-      const R h1 = Ha[c];
-      const R h2 = M.H[(int64_t)c * d + b];
-      const C x = wn[(int64_t)c * d + b];
-      const C z = wn[(int64_t)a * d + c];
-      re += h1 * x.x - z.x * h2;
-      im += h1 * x.y - z.y * h2;
-    }
-    // -i [H, w]
-    R ore = im, oim = -re;
-    const R dec = (R)M.decay[n];
-    const C self = wn[el];
-    ore -= dec * self.x;
-    oim -= dec * self.y;
-    for (int s = 0; s < M.n_modes; ++s) {
-      const int o0 = M.nb_off[n * M.n_modes + s], o1 = M.nb_off[n * M.n_modes + s + 1];
-      if (o0 == o1) continue;
-      const int ns = M.dims[s], st = M.stride[s];
-      const int as = (a / st) % ns, bs = (b / st) % ns;
-      const int abase = a - as * st, bbase = b - bs * st;
-      const R *V = M.vloc + M.vloc_off[s];
-      for (int q = o0; q < o1; ++q) {
-        const C *wm = wb + (int64_t)M.nb_idx[q] * dd;
-        R lx = 0, ly = 0, rx = 0, ry = 0;
-        for (int k = 0; k < ns; ++k) {
-          const R vl = V[as * ns + k];
-          const C xl = wm[(int64_t)(abase + k * st) * d + b];
-          lx += vl * xl.x;
-          ly += vl * xl.y;
-          const R vr = V[k * ns + bs];
-          const C xr = wm[(int64_t)a * d + bbase + k * st];
-          rx += xr.x * vr;
-          ry += xr.y * vr;
-        }
-        const R cA = M.nb_cA[q], cB = M.nb_cB[q];
-        ore += cA * (ly - ry) + cB * (lx + rx);
-        oim += -cA * (lx - rx) + cB * (ly + ry);
-      }
-    }
-    const C yv = y[e];
-    C o;
-    o.x = yv.x + alpha * ore;
-    o.y = yv.y + alpha * oim;
-    out[e] = o;
+    int k = 0;
+    while (k + 1 < n_sets && e >= sets[k + 1].begin) ++k;
+    const SetStage<R> &S = sets[k];
+    stage_element<R>(S.w, S.y, S.out, alpha, S.M, e - S.begin);
   }
 }
 

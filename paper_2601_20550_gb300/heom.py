@@ -86,6 +86,8 @@ def lib():
         "heom_response_2d_rows": [_P, _P, ct.POINTER(heom_grid), ct.c_int, ct.c_int, _D, _D],
         "heom_response_2d_batched": [ct.POINTER(_P), ct.POINTER(_P), ct.c_int, ct.POINTER(heom_grid), _D, _D, _D],
         "heom_response_2d_grad": [_P, _P, ct.POINTER(heom_grid), _D, ct.c_int, _D, _D],
+        "heom_get_tuning": [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int),
+                            ct.POINTER(ct.c_int)],
         "heom_state_broadcast": [_P, _P],
         "heom_spectrum_2d": [_D, _D, ct.c_int, ct.c_int, ct.c_int, ct.c_double, _D],
         "heom_trace_dev": [_P, _P, ct.c_int, ct.c_int, ct.c_int, _P, _P],
@@ -388,6 +390,16 @@ def heom_propagate_noalloc(h, state_ptr, branches, dt_fs, n_steps, stream_ptr=0)
     """Allocation-free FP64 propagation of a device state (scratch in a static device array)."""
     _check(lib().heom_propagate_noalloc(h.h, _P(state_ptr), branches, dt_fs, int(n_steps),
                                         _P(stream_ptr)))
+
+
+def heom_get_tuning(h):
+    """[(kind, elements, block, grid)] launch shapes the autotuner chose for hierarchy h."""
+    L = lib()
+    n = L.heom_get_tuning(h.h, 0, None, None, None, None)
+    kind, el = (ct.c_int * max(n, 1))(), (ct.c_int64 * max(n, 1))()
+    blk, grd = (ct.c_int * max(n, 1))(), (ct.c_int * max(n, 1))()
+    L.heom_get_tuning(h.h, n, kind, el, blk, grd)
+    return [(kind[i], el[i], blk[i], grd[i]) for i in range(n)]
 
 
 def heom_launch_count():

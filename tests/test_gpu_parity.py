@@ -302,3 +302,54 @@ def test_response_2d_degenerate_grids(precision, tol, n1, n3, depth_L):
     assert np.abs(RI - RIo).max() < tol * scale
     assert np.abs(RII - RIIo).max() < tol * scale
     assert np.abs(SC - SCo).max() <= tol * np.abs(SCo).max() + 1e-300
+
+
+@pytest.mark.gpu
+def test_autotuner_picks_a_shape_once():
+    """The first propagation of a size tunes the stage-kernel launch; later ones reuse it."""
+    model = W.small_two_mode(n1=3, n2=3, depth_L=2)
+    h = H.heom_build_hierarchy(model, H.FP64)
+    s = H.heom_state_create(h, 3, H.FP64)
+    H.heom_state_upload(s, rand_state((3, h.n_ado, h.d, h.d), 4, hermitian=True))
+    H.heom_propagate(h, s, 0.5, 4)
+    first = H.heom_get_tuning(h)
+    total = 3 * h.n_ado * h.d * h.d
+    entry = [e for e in first if e[0] == 0 and e[1] == total]
+    assert len(entry) == 1 and entry[0][2] in (64, 128, 256) and entry[0][3] >= 1
+    H.heom_propagate(h, s, 0.5, 4)
+    assert H.heom_get_tuning(h) == first
+
+
+@pytest.mark.gpu
+def test_batched_one_launch_equals_per_set():
+    """Three FP64 sets of different basis size advanced together match per-set calls."""
+    grid = W.grid(0.5, 3, 5, 4, (0.0, 2.0), t_eq_fs=12.0)
+    models = [W.small_two_mode(n1=3, n2=3, depth_L=2), W.small_three_mode(n=2, depth_L=2),
+              W.small_two_mode(n1=4, n2=3, depth_L=3)]
+    hs = [H.heom_build_hierarchy(m) for m in models]
+    eqs = [H.heom_equilibrate(h, grid["dt_fs"], grid["t_eq_fs"], 0.0) for h in hs]
+    assert len({h.d for h in hs}) == 3
+    n0 = H.heom_launch_count()
+    RI, RII, SC = H.heom_response_2d_batched(hs, eqs, grid)
+    launches_batched = H.heom_launch_count() - n0
+    n0 = H.heom_launch_count()
+    for i, (h, eq) in enumerate(zip(hs, eqs)):
+        ri, rii, sc = H.heom_response_2d(h, eq, grid)
+        scale = max(np.abs(ri).max(), np.abs(rii).max())
+        assert np.abs(RI[i] - ri).max() <= 1e-14 * scale
+        assert np.abs(RII[i] - rii).max() <= 1e-14 * scale
+        assert np.abs(SC[i] - sc).max() <= 1e-14 * np.abs(sc).max()
+    launches_single = H.heom_launch_count() - n0
+    assert launches_batched < launches_single
+
+
+@pytest.mark.gpu
+def test_batched_mixed_precision_sets_fall_back():
+    grid = W.grid(0.5, 4, 6, 6, (0.0,), t_eq_fs=20.0)
+    models = [W.small_three_mode(n=3, depth_L=2), W.small_three_mode(n=2, depth_L=2)]
+    hs = [H.heom_build_hierarchy(m, H.TC) for m in models]
+    eqs = [H.heom_equilibrate(h, 0.5, 20.0, 0.0) for h in hs]
+    RI, RII, SC = H.heom_response_2d_batched(hs, eqs, grid)
+    for i, m in enumerate(models):
+        _, RIo, RIIo, SCo = OH.spectrum_2d(OM.Problem(m), grid)
+        assert np.abs(SC[i] - SCo).max() < 1e-4 * np.abs(SCo).max()
