@@ -192,6 +192,26 @@ heom_status heom_response_2d(heom_hier *h, const heom_state *rho_eq, const heom_
                              double *R_I, double *R_II, double *S_C);
 
 /*
+ * Stationary hierarchy by a Krylov solve instead of propagation (the steady
+ * state that the equilibration of Sec. II.C.1 approaches): restarted
+ * GMRES(restart) from x = |0><0| on A x = 0 with A = L (the right-hand side of
+ * Eq. HEOM_DB, FP64, product basis) when steps_per_matvec = 0, or A = G^k - 1
+ * with G one RK4 step of dt_fs and k = steps_per_matvec.  Both have the steady
+ * state as null vector; the second compresses the spectrum of a stiff hierarchy
+ * (fast coherences, slow population transfer) into a range GMRES handles in a
+ * few hundred products.  Every correction lies in the range of A, where
+ * tr(.)_0 vanishes because the HEOM conserves tr rho_0, so tr x_0 = 1
+ * throughout.  Stops when ||L x||_2 <= tol (checked at every restart); at most
+ * max_iter Arnoldi steps (HEOM_ENOTCONV with the last iterate in *rho_eq
+ * otherwise).  Memory: restart + 5 vectors of n_ado d^2 complex128.  *rho_eq is
+ * a single-branch FP64 state usable wherever an equilibrium is taken, except
+ * heom_response_2d_grad (which replays a propagation).  *iterations (may be
+ * NULL) receives the Arnoldi steps taken.
+ */
+heom_status heom_steady_state(heom_hier *h, double tol, int restart, int max_iter, double dt_fs,
+                              int steps_per_matvec, heom_state **rho_eq, int *iterations);
+
+/*
  * Launch shapes chosen by the library's autotuner (no counterpart in the paper:
  * a tuning aid).  The first RK4 propagation of a given size on the FP64
  * (kind 0) or FP32 coupling-basis (kind 1) path times nine launch shapes of its

@@ -14,6 +14,8 @@ Pins (tests/test_oracle_heom.py, tests/test_oracle_physics.py):
     third-order response of the harmonic oscillator; one-sided kicks on |0><0|.
   * equilibrate: thermal <q^2> of a low-frequency oscillator (Matsubara / Pade sum);
     null vector of the Liouvillian.
+  * steady_state: the null vector of the independently assembled Liouvillian and the
+    long-time limit of the propagation.
   * dft2d / correlation spectrum: brute-force single-frequency signals.
 """
 import math
@@ -104,6 +106,31 @@ def equilibrate(prob, dt, t_eq_fs=None, tol=None, t_max_fs=None, check_every=100
         if res <= tol * np.linalg.norm(rho[0, 0]):
             return rho, steps, True
     return rho, steps, False
+
+
+def steady_state(prob):
+    """Stationary hierarchy by a direct solve (alternative to the propagation of Sec. II.C.1).
+
+    The definition written out: L x = 0 with tr x_0 = 1, where L is the
+    right-hand side of Eq. HEOM_DB as a matrix on vec(rho).  L is built column by
+    column from ``rhs`` applied to unit states (tiny problems only), the first
+    equation is replaced by the trace condition, and the dense system is solved.
+    """
+    shape = (1, prob.nado, prob.d, prob.d)
+    n = prob.nado * prob.d * prob.d
+    L = np.zeros((n, n), dtype=complex)
+    e = np.zeros(n, dtype=complex)
+    for k in range(n):
+        e[k] = 1.0
+        L[:, k] = rhs(prob, e.reshape(shape)).reshape(n)
+        e[k] = 0.0
+    A = L.copy()
+    b = np.zeros(n, dtype=complex)
+    A[0, :] = 0.0
+    for a in range(prob.d):
+        A[0, a * prob.d + a] = 1.0
+    b[0] = 1.0
+    return np.linalg.solve(A, b).reshape(shape)
 
 
 def kick(rho, M):

@@ -86,6 +86,8 @@ def lib():
         "heom_response_2d_rows": [_P, _P, ct.POINTER(heom_grid), ct.c_int, ct.c_int, _D, _D],
         "heom_response_2d_batched": [ct.POINTER(_P), ct.POINTER(_P), ct.c_int, ct.POINTER(heom_grid), _D, _D, _D],
         "heom_response_2d_grad": [_P, _P, ct.POINTER(heom_grid), _D, ct.c_int, _D, _D],
+        "heom_steady_state": [_P, ct.c_double, ct.c_int, ct.c_int, ct.c_double, ct.c_int, ct.POINTER(_P),
+                              ct.POINTER(ct.c_int)],
         "heom_get_tuning": [_P, ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int),
                             ct.POINTER(ct.c_int)],
         "heom_state_broadcast": [_P, _P],
@@ -390,6 +392,17 @@ def heom_propagate_noalloc(h, state_ptr, branches, dt_fs, n_steps, stream_ptr=0)
     """Allocation-free FP64 propagation of a device state (scratch in a static device array)."""
     _check(lib().heom_propagate_noalloc(h.h, _P(state_ptr), branches, dt_fs, int(n_steps),
                                         _P(stream_ptr)))
+
+
+def heom_steady_state(h, tol=1e-12, restart=40, max_iter=4000, dt_fs=0.5, steps_per_matvec=0):
+    """(rho_eq State, Arnoldi steps) of the Krylov steady-state solve."""
+    out = _P()
+    its = ct.c_int(0)
+    rc = _check(lib().heom_steady_state(h.h, float(tol), int(restart), int(max_iter), float(dt_fs),
+                                        int(steps_per_matvec), ct.byref(out), ct.byref(its)), allow=(-6,))
+    s = State(out, h, 1, FP64)
+    s.converged = rc == 0
+    return s, its.value
 
 
 def heom_get_tuning(h):

@@ -353,3 +353,32 @@ def test_batched_mixed_precision_sets_fall_back():
     for i, m in enumerate(models):
         _, RIo, RIIo, SCo = OH.spectrum_2d(OM.Problem(m), grid)
         assert np.abs(SC[i] - SCo).max() < 1e-4 * np.abs(SCo).max()
+
+
+@pytest.mark.gpu
+def test_steady_state_krylov():
+    """GMRES steady state against the oracle's direct null-vector solve."""
+    model = W.harmonic_bo(omega_cm=300.0, n_levels=5, lambda_cm=60.0, gamma_cm=150.0,
+                          depth_L=2, K_pade=1)
+    model["modes"][0]["g3_cm"] = -40.0
+    model["modes"][0]["n_prim"] = 12
+    model["modes"][0]["V_SL"] = 0.2
+    x = OH.steady_state(OM.Problem(model))
+    h = H.heom_build_hierarchy(model)
+    s, its = H.heom_steady_state(h, tol=1e-12, restart=30, max_iter=3000)
+    assert s.converged and its > 0
+    got = H.heom_state_download(s)
+    assert np.max(np.abs(got - x)) < 1e-9 * np.max(np.abs(x))
+
+
+@pytest.mark.gpu
+def test_steady_state_two_modes():
+    """A two-mode model whose slowest relaxation takes ~4e4 fs (stiff for propagation)."""
+    model = W.small_two_mode(n1=3, n2=3, depth_L=2)
+    x = OH.steady_state(OM.Problem(model))
+    h = H.heom_build_hierarchy(model)
+    s, its = H.heom_steady_state(h, tol=1e-12, restart=60, max_iter=900, dt_fs=0.5, steps_per_matvec=2000)
+    assert s.converged, its
+    a = H.heom_state_download(s)
+    assert abs(np.trace(a[0, 0]) - 1.0) < 1e-10
+    assert np.max(np.abs(a - x)) < 1e-8 * np.max(np.abs(x))

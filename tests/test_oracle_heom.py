@@ -124,6 +124,25 @@ def test_equilibrium_is_null_vector():
     assert np.max(np.abs(rho - x)) < 1e-8 * np.max(np.abs(x))
 
 
+def test_steady_state_direct_solve():
+    """oracle.steady_state against the independently assembled Liouvillian's null
+    vector, the propagated equilibrium, and the trace and Hermiticity it must carry."""
+    model = W.harmonic_bo(omega_cm=300.0, n_levels=5, lambda_cm=60.0, gamma_cm=150.0,
+                          depth_L=2, K_pade=1)
+    model["modes"][0]["g3_cm"] = -40.0
+    model["modes"][0]["n_prim"] = 12
+    model["modes"][0]["V_SL"] = 0.2
+    prob = M.Problem(model)
+    x = Hm.steady_state(prob)
+    L = liouvillian(prob)
+    v = x.reshape(-1)
+    assert np.max(np.abs(L @ v)) < 1e-10 * np.max(np.abs(v))
+    assert abs(np.trace(x[0, 0]) - 1.0) < 1e-12
+    assert np.max(np.abs(x[0, 0] - x[0, 0].conj().T)) < 1e-10
+    rho, _, conv = Hm.equilibrate(prob, 1.0, tol=1e-11, t_max_fs=20000.0, check_every=500)
+    assert conv and np.max(np.abs(rho - x)) < 1e-8 * np.max(np.abs(x))
+
+
 def test_first_kick_on_ground_state():
     prob = M.Problem(W.small_two_mode())
     rho = Hm.initial_state(prob)
