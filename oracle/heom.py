@@ -33,8 +33,8 @@ def acomm(A, X):
     return A @ X + X @ A
 
 
-def rhs(prob, rho):
-    """Eq. HEOM_DB for every ADO of every branch.
+def rhs_one(prob, get, i):
+    """Eq. HEOM_DB for ADO i alone; get(k) returns ADO k of every branch, shape (B, d, d).
 
     d rho_n/dt = -(i H_S'^x + sum_j n_j nu_j) rho_n
                  - i sum_j n_j Theta_j rho_{n - e_j}
@@ -43,23 +43,28 @@ def rhs(prob, rho):
     index set.
     """
     sysm, bath, hier = prob.sys, prob.bath, prob.hier
-    H = sysm.H
+    n = hier.n[i]
+    r = get(i)
+    decay = sum(n[j] * bath.nu[j] for j in range(hier.D))
+    acc = -1j * comm(sysm.H, r) - decay * r
+    for j in range(hier.D):
+        Vs = sysm.V[bath.mode_of[j]]
+        dn = hier.down(i, j)
+        if dn >= 0:
+            rd = get(dn)
+            theta = bath.a[j] * comm(Vs, rd) + bath.b[j] * acomm(Vs, rd)
+            acc = acc - 1j * n[j] * theta
+        up = hier.up(i, j)
+        if up >= 0:
+            acc = acc - 1j * comm(Vs, get(up))
+    return acc
+
+
+def rhs(prob, rho):
+    """Eq. HEOM_DB for every ADO of every branch (``rhs_one`` over the index set)."""
     out = np.empty_like(rho)
-    for i, n in enumerate(hier.n):
-        r = rho[:, i]
-        decay = sum(n[j] * bath.nu[j] for j in range(hier.D))
-        acc = -1j * comm(H, r) - decay * r
-        for j in range(hier.D):
-            Vs = sysm.V[bath.mode_of[j]]
-            dn = hier.down(i, j)
-            if dn >= 0:
-                rd = rho[:, dn]
-                theta = bath.a[j] * comm(Vs, rd) + bath.b[j] * acomm(Vs, rd)
-                acc = acc - 1j * n[j] * theta
-            up = hier.up(i, j)
-            if up >= 0:
-                acc = acc - 1j * comm(Vs, rho[:, up])
-        out[:, i] = acc
+    for i in range(prob.nado):
+        out[:, i] = rhs_one(prob, lambda k: rho[:, k], i)
     return out
 
 

@@ -208,7 +208,8 @@ static void stability_check(heom_hier *h, double dt) {
 // a kernel kind at a given size times every candidate (block of 64, 128 or 256
 // threads; 4, 16 or 64 blocks per SM, capped at one element per thread) on the
 // real operands -- three timed launches each after one untimed -- and keeps the
-// fastest for this hierarchy.  Candidate launches repeat the caller's first
+// fastest for this hierarchy; a size whose default launch already takes over
+// 50 ms keeps the default.  Candidate launches repeat the caller's first
 // stage, whose output is scratch that the step overwrites next, so tuning
 // changes no result.  Inside a stream capture, or when timing fails, the
 // default shape (256 threads, grid_for) is used and nothing is cached.
@@ -230,6 +231,22 @@ static std::pair<int, int> tuned_shape(heom_hier *h, int kind, int64_t total, cu
   std::pair<int, int> best = dflt;
   float best_ms = 1e30f;
   bool ok = true;
+  {
+    // one launch of the default shape first: launches longer than 50 ms are
+    // saturated by their size and not worth 36 more, so the default is kept
+    float ms = 0.f;
+    cudaEventRecord(e0, st);
+    launch(dflt.first, dflt.second);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ok = false;
+    if (ok && ms > 50.f) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      LAUNCH_CHECK();
+      h->tuned[{kind, total}] = dflt;
+      return dflt;
+    }
+  }
   for (int block : {64, 128, 256})
     for (int per_sm : {4, 16, 64}) {
       const int64_t need = (total + block - 1) / block;

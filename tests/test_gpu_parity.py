@@ -382,3 +382,56 @@ def test_steady_state_two_modes():
     a = H.heom_state_download(s)
     assert abs(np.trace(a[0, 0]) - 1.0) < 1e-10
     assert np.max(np.abs(a - x)) < 1e-8 * np.max(np.abs(x))
+
+
+def _neighbours(hier, ados):
+    out = set(ados)
+    for i in ados:
+        for j in range(hier.D):
+            for f in (hier.up, hier.down):
+                k = f(i, j)
+                if k >= 0:
+                    out.add(k)
+    return out
+
+
+@pytest.mark.gpu
+def test_c5_full_size_step_sampled():
+    """c5 at full size (d = 216, 24310 ADOs, 18 GB per FP64 state): one RK4 step of a
+    state that is non-zero on one ADO, against the oracle's classic RK4 evaluated on the
+    dependency cone of that ADO (per-ADO right-hand sides); a distant ADO stays zero."""
+    torch = pytest.importorskip("torch")
+    model, grid = W.config("c5")
+    h = H.heom_build_hierarchy(model, H.FP64)
+    prob = OM.Problem(model)
+    hier, dt = prob.hier, grid["dt_fs"]
+    n = 5000
+    rng = np.random.default_rng(55)
+    x = (rng.standard_normal((h.d, h.d)) + 1j * rng.standard_normal((h.d, h.d)))[None]
+    y = torch.zeros((1, h.n_ado, h.d, h.d), dtype=torch.complex128, device="cuda")
+    y[0, n].copy_(torch.from_numpy(x[0]))
+    wa, wb = torch.empty_like(y), torch.empty_like(y)
+    H.heom_propagate_dev(h, y.data_ptr(), wa.data_ptr(), wb.data_ptr(), 1, H.FP64, dt, 1,
+                         torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    got = y[0, n].cpu().numpy()
+    N1 = _neighbours(hier, {n})
+    N2 = _neighbours(hier, N1)
+    far = next(i for i in range(h.n_ado) if i not in _neighbours(hier, _neighbours(hier, N2)))
+    assert float(y[0, far].abs().max()) == 0.0
+    del y, wa, wb
+    zero = np.zeros_like(x)
+    yv = {n: x}
+
+    def getter(d):
+        return lambda k: d.get(k, zero)
+
+    k1 = {m: OH.rhs_one(prob, getter(yv), m) for m in N1}
+    u2 = {m: yv.get(m, zero) + 0.5 * dt * k1[m] for m in N1}
+    k2 = {m: OH.rhs_one(prob, getter(u2), m) for m in N2}
+    u3 = {m: yv.get(m, zero) + 0.5 * dt * k2[m] for m in N2}
+    k3 = {m: OH.rhs_one(prob, getter(u3), m) for m in N1}
+    u4 = {m: yv.get(m, zero) + dt * k3[m] for m in N1}
+    k4 = OH.rhs_one(prob, getter(u4), n)
+    ref = (x + dt / 6.0 * (k1[n] + 2 * k2[n] + 2 * k3[n] + k4))[0]
+    assert rel(got, ref) < 1e-11
