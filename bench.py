@@ -39,6 +39,7 @@ WORKLOADS = {
     "c3-fp64": ("c3", 0, 2),
     "c1-fp64": ("c1", 0, 64),
     "c4-grad": ("c4", 0, 0),       # adjoint gradient of the spectrum misfit (own JSON line)
+    "c5-window": ("c5", 0, 0),     # c5 RK4 steps on a few branches, projected spectra/hour
 }
 PREC_NAME = {0: "f64", 1: "f32", 2: "fp16x2-tc-f32acc"}
 
@@ -250,6 +251,48 @@ def run_grad(args, local):
         "dtheta": list(map(float, g)), "gpu_launches": int(launches)}))
 
 
+def run_c5_window(args, local):
+    """c5 (d = 216, 24310 ADOs) on a window: --steps RK4 steps of --branches branches
+    (default 2) after --warmup steps, FP64 (--c5-precision 0) or FP32 coupling basis (1),
+    device-timed; spectra/hour projected from ADO-updates per spectrum (t2 = 0).  The
+    state is a kicked unit hierarchy (timing does not depend on the values)."""
+    import torch
+    torch.cuda.set_device(local)
+    from paper_2601_20550_gb300 import heom as H
+    model, grid = W.config("c5")
+    prec = args.c5_precision
+    h = H.heom_build_hierarchy(model, prec)
+    d, nado = h.d, h.n_ado
+    B = args.branches if args.branches > 0 else 2
+    cdt = torch.complex128 if prec == 0 else torch.complex64
+    y = torch.zeros((B, nado, d, d), dtype=cdt, device="cuda")
+    y[:, 0, 0, 1] = 1.0
+    y[:, 0, 1, 0] = 1.0
+    wa, wb = torch.empty_like(y), torch.empty_like(y)
+    sp = torch.cuda.current_stream().cuda_stream
+    for _ in range(args.warmup):
+        H.heom_propagate_dev(h, y.data_ptr(), wa.data_ptr(), wb.data_ptr(), B, prec, grid["dt_fs"], 1, sp)
+    torch.cuda.synchronize()
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = H.heom_launch_count()
+    s.record()
+    H.heom_propagate_dev(h, y.data_ptr(), wa.data_ptr(), wb.data_ptr(), B, prec, grid["dt_fs"], args.steps, sp)
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / args.steps
+    value = B * nado / (ms / 1e3)
+    per_spec = ado_updates_per_spectrum(grid, nado)
+    print(json.dumps({
+        "metric": "HEOM ADO-updates/s (c5 window, projected 2D spectra/hour)", "value": value,
+        "unit": "ADO-updates/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "dtype": "f64" if prec == 0 else "f32",
+        "data": "synthetic (seeded water-like MAB model; no dataset)",
+        "config": {"workload": "c5: 3-mode MAB, d=%d, %d ADOs (L=8, K_s=2), %d branches, dt=0.25 fs"
+                               % (d, nado, B), "state_GB": B * nado * d * d * (16 if prec == 0 else 8) / 1e9},
+        "projected_spectra_per_hour": 3600.0 * value / per_spec, "ado_updates_per_spectrum": per_spec,
+        "gpu_launches": int(H.heom_launch_count() - n0)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -263,6 +306,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--grad-n", type=int, default=16, help="t1 and t3 samples of the c4-grad workload")
+    ap.add_argument("--c5-precision", type=int, default=0, choices=[0, 1], help="c5-window: 0 FP64, 1 FP32")
     ap.add_argument("--branches", type=int, default=0,
                     help="override the batch (profiling runs only; default 2*n1)")
     args = ap.parse_args()
@@ -277,6 +321,10 @@ def main():
     if args.workload == "c4-grad":
         if rank == 0:
             run_grad(args, local)
+        return
+    if args.workload == "c5-window":
+        if rank == 0:
+            run_c5_window(args, local)
         return
 
     import torch
