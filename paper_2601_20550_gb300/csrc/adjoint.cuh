@@ -48,12 +48,14 @@ __global__ void __launch_bounds__(256) neg_dagger_kernel(const double2 *__restri
 // Commutator-type gradient: for every item (ADO matrix) i,
 //   G[p][q] += alpha Re[ phase ( sum_b conj(g_i[p][b]) w_i[q][b] - sum_a w_i[a][p] conj(g_i[a][q]) ) ],
 // the derivative of Re <g, phase^* ... > with respect to a matrix K in K^x w
-// (phase = -i for the Hamiltonian term -i[H, w], 1 for a kick K^x w).
+// (phase = -i for the Hamiltonian term -i[H, w], 1 for a kick K^x w).  Only the
+// component the phase selects is accumulated: the imaginary part for -i, the real
+// part for 1 (half the arithmetic of the full complex product).
 // Block = 16 x 16 entries of G, looping over a chunk of items with 16-wide
 // slices of the contraction index staged in shared memory.
+template <bool kImag>
 __global__ void __launch_bounds__(256) comm_grad_kernel(const double2 *__restrict__ g, const double2 *__restrict__ w,
-                                                        int64_t n_items, int d, double ph_re, double ph_im,
-                                                        double alpha, double *__restrict__ G) {
+                                                        int64_t n_items, int d, double alpha, double *__restrict__ G) {
   __shared__ double2 sg1[16][17], sw1[16][17], sw2[16][17], sg2[16][17];
   const int tiles = (d + 15) / 16;
   const int tile = blockIdx.x % (tiles * tiles);
@@ -62,7 +64,7 @@ __global__ void __launch_bounds__(256) comm_grad_kernel(const double2 *__restric
   const int p0 = (tile / tiles) * 16, q0 = (tile % tiles) * 16;
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
   const int64_t dd = (int64_t)d * d;
-  double ar = 0.0, ai = 0.0;
+  double acc = 0.0;
   for (int64_t i = chunk; i < n_items; i += n_chunks) {
     const double2 *gi = g + i * dd, *wi = w + i * dd;
     for (int k0 = 0; k0 < d; k0 += 16) {
@@ -75,20 +77,18 @@ __global__ void __launch_bounds__(256) comm_grad_kernel(const double2 *__restric
       __syncthreads();
 #pragma unroll
       for (int kk = 0; kk < 16; ++kk) {
-        // conj(g[p][k]) w[q][k]
-        const double2 a1 = sg1[ty][kk], b1 = sw1[tx][kk];
-        ar += a1.x * b1.x + a1.y * b1.y;
-        ai += a1.x * b1.y - a1.y * b1.x;
-        // - w[k][p] conj(g[k][q])
-        const double2 a2 = sw2[kk][ty], b2 = sg2[kk][tx];
-        ar -= a2.x * b2.x + a2.y * b2.y;
-        ai -= a2.y * b2.x - a2.x * b2.y;
+        const double2 a1 = sg1[ty][kk], b1 = sw1[tx][kk];   // conj(g[p][k]) w[q][k]
+        const double2 a2 = sw2[kk][ty], b2 = sg2[kk][tx];   // w[k][p] conj(g[k][q])
+        if (kImag)
+          acc += (a1.x * b1.y - a1.y * b1.x) - (a2.y * b2.x - a2.x * b2.y);
+        else
+          acc += (a1.x * b1.x + a1.y * b1.y) - (a2.x * b2.x + a2.y * b2.y);
       }
       __syncthreads();
     }
   }
   const int p = p0 + ty, q = q0 + tx;
-  if (p < d && q < d) atomicAdd(G + (int64_t)p * d + q, alpha * (ph_re * ar - ph_im * ai));
+  if (p < d && q < d) atomicAdd(G + (int64_t)p * d + q, alpha * acc);
 }
 
 // Gradients of the system-bath and decay terms of L (Eq. HEOM_DB) for one pair

@@ -1391,7 +1391,13 @@ static void comm_grad(AdjCtx &c, const double2 *g, const double2 *w, int64_t ite
                       double alpha, double *G) {
   const int d = c.h->M.d, tiles = (d + 15) / 16;
   const int64_t chunks = std::max<int64_t>(1, std::min<int64_t>(items, std::max(1, 2432 / (tiles * tiles))));
-  comm_grad_kernel<<<(unsigned)(tiles * tiles * chunks), 256, 0, c.st>>>(g, w, items, d, ph_re, ph_im, alpha, G);
+  // Re(-i x) = Im x (Hamiltonian term); Re(1 x) = Re x (kicks)
+  if (ph_re == 0.0 && ph_im == -1.0)
+    comm_grad_kernel<true><<<(unsigned)(tiles * tiles * chunks), 256, 0, c.st>>>(g, w, items, d, alpha, G);
+  else if (ph_re == 1.0 && ph_im == 0.0)
+    comm_grad_kernel<false><<<(unsigned)(tiles * tiles * chunks), 256, 0, c.st>>>(g, w, items, d, alpha, G);
+  else
+    throw Fail{HEOM_EINVAL, "unsupported gradient phase"};
   count_launch(1);
   LAUNCH_CHECK();
 }
