@@ -11,8 +11,9 @@
 //   2. one thread of warp 16 issues tcgen05.mma: D = Z^T H' - H' Z^T = [H', Z]^T
 //      with the H' pieces (hi, mid, lo) resident in shared memory and FP32
 //      accumulation in tensor memory (256 columns: Re D | Im D, double-buffered),
-//      in two commit groups so the lo tiles are released before the hi products
-//      finish;
+//      in two commit groups: the products with the hi tiles as soon as those are
+//      written (their completion frees the hi tiles for the next item), then the
+//      product with the lo tiles;
 //   3. epilogue warps 12-15 read D from tensor memory (lane = column b of w_n,
 //      column = row a) and store tpart = alpha (-i C) with coalesced accesses.
 // vterm_kernel then adds y, tpart and the elementwise decay and system-bath
@@ -154,13 +155,14 @@ __device__ __forceinline__ float item_scale(unsigned mbits) {
 }
 
 // Warp-specialised persistent stage kernel.
-//   warps 0-11 (producers): per item, wait until the previous item's first MMA
-//              group has released the lo tiles, load and split w_n (lo parts to
-//              the tiles, hi parts held in registers), wait for the remaining
-//              MMAs, write the hi parts and signal the tiles ready.
-//   warp 16    (MMA issue): per item, wait for the tiles and for the
-//              tensor-memory buffer of the item's parity, issue the MMAs in two
-//              commit groups.  Issue blocks while the tensor cores drain the
+//   warps 0-11 (producers): per item, load the first half of w_n, wait until the
+//              previous item's first MMA group has released the hi tiles, split
+//              w_n (hi parts to the tiles, signalled at once; lo parts held in
+//              registers), wait for the previous item's last MMA group, write the
+//              lo parts and signal them.
+//   warp 16    (MMA issue): per item, wait for the hi tiles and for the
+//              tensor-memory buffer of the item's parity, issue the hi-tile MMAs,
+//              wait for the lo tiles, issue the lo-tile MMA group.  Issue blocks while the tensor cores drain the
 //              queue, so it runs in its own warp and the producers convert the
 //              next item meanwhile.
 //   warps 12-15 (epilogue): per item, wait for the MMAs, read the accumulator,
@@ -168,7 +170,7 @@ __device__ __forceinline__ float item_scale(unsigned mbits) {
 // The epilogue of item k overlaps the MMAs of item k + 1 and the loads of k + 2.
 __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t bar_mma[2], bar_lo[2], bar_full[2], bar_epi[2], bar_ready[2];
+  __shared__ uint64_t bar_mma[2], bar_hi[2], bar_full[2], bar_epi[2], bar_ready_hi[2], bar_ready_lo[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
 
@@ -184,10 +186,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
     s_abort = 0;
     for (int t = 0; t < 2; ++t) {
       mbar_init(&bar_mma[t], 1);
-      mbar_init(&bar_lo[t], 1);
+      mbar_init(&bar_hi[t], 1);
       mbar_init(&bar_full[t], 1);
       mbar_init(&bar_epi[t], kEpilogue / 32);
-      mbar_init(&bar_ready[t], kProducers / 32);
+      mbar_init(&bar_ready_hi[t], kProducers / 32);
+      mbar_init(&bar_ready_lo[t], kProducers / 32);
     }
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
@@ -244,15 +247,16 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       load_batch(0);
       // power-of-two scale from the item's largest component (kept by the previous stage)
       const float scale = item_scale(P.max_in[item]);
-      // The lo tiles are free once the previous item's first MMA group (the
-      // products with Z2) has completed; every producer reaches the barrier, then
+      // The hi tiles are free once the previous item's first MMA group (the
+      // products with Z1) has completed; every producer reaches the barrier, then
       // all read the abort flag (uniform exit).
-      if (k >= 1) mbar_wait(&bar_lo[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort);
+      if (k >= 1) mbar_wait(&bar_hi[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort);
       producer_sync();
       if (*(volatile int *)&s_abort) break;
-      // scale and split into FP16 hi + lo; lo goes to the tiles now, hi is kept in
-      // registers until the previous item's remaining MMAs (with Z1) are done
-      __half2 hre[2 * kProdRows], him[2 * kProdRows];
+      // scale and split into FP16 hi + lo; hi goes to the tiles now (the MMA warp
+      // starts the hi products as soon as they are all written), lo is kept in
+      // registers until the previous item's last MMA group (with Z2) is done
+      __half2 lre[2 * kProdRows], lim[2 * kProdRows];
 #pragma unroll
       for (int bt = 0; bt < 2; ++bt) {
         if (bt == 1) load_batch(1);
@@ -262,30 +266,33 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
           const float2 xr = make_float2(v[2 * i].x * scale, v[2 * i + 1].x * scale);
           const float2 xi = make_float2(v[2 * i].y * scale, v[2 * i + 1].y * scale);
           const __half2 hr = __float22half2_rn(xr), hi = __float22half2_rn(xi);
-          hre[g] = hr;
-          him[g] = hi;
+          const float2 fr = __half22float2(hr), fi = __half22float2(hi);
+          lre[g] = __float22half2_rn(make_float2(xr.x - fr.x, xr.y - fr.y));
+          lim[g] = __float22half2_rn(make_float2(xi.x - fi.x, xi.y - fi.y));
           if (active && r0 + 6 * g < d) {
-            const float2 fr = __half22float2(hr), fi = __half22float2(hi);
             const uint32_t o = row_ofs[g & 3] + 3072u * (uint32_t)(g >> 2);
-            *reinterpret_cast<__half2 *>(ZZ2 + o) = __float22half2_rn(make_float2(xr.x - fr.x, xr.y - fr.y));
-            *reinterpret_cast<__half2 *>(ZZ2 + o + 16384u) = __float22half2_rn(make_float2(xi.x - fi.x, xi.y - fi.y));
+            *reinterpret_cast<__half2 *>(ZZ1 + o) = hr;
+            *reinterpret_cast<__half2 *>(ZZ1 + o + 16384u) = hi;
           }
         }
       }
-      // the hi tiles are free once the previous item's MMAs have all completed
+      asm volatile("fence.proxy.async.shared::cta;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&bar_ready_hi[t]);
+      // the lo tiles are free once the previous item's MMAs have all completed
       if (k >= 1) mbar_wait(&bar_mma[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort);
       if (active) {
 #pragma unroll
         for (int g = 0; g < 2 * kProdRows; ++g)
           if (r0 + 6 * g < d) {
             const uint32_t o = row_ofs[g & 3] + 3072u * (uint32_t)(g >> 2);
-            *reinterpret_cast<__half2 *>(ZZ1 + o) = hre[g];
-            *reinterpret_cast<__half2 *>(ZZ1 + o + 16384u) = him[g];
+            *reinterpret_cast<__half2 *>(ZZ2 + o) = lre[g];
+            *reinterpret_cast<__half2 *>(ZZ2 + o + 16384u) = lim[g];
           }
       }
       asm volatile("fence.proxy.async.shared::cta;");
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bar_ready[t]);
+      if (lane == 0) mbar_arrive(&bar_ready_lo[t]);
     }
   } else if (warp < kMmaWarp) {
     // ------------------------------------------------------------ epilogue
@@ -335,16 +342,20 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
         const int t = (int)(k & 1);
         // the tiles of item k are written; its accumulator buffer is free once
         // the epilogue of item k - 2 released it
-        bool ok = mbar_wait(&bar_ready[t], (uint32_t)((k >> 1) & 1), op.err, &s_abort);
+        bool ok = mbar_wait(&bar_ready_hi[t], (uint32_t)((k >> 1) & 1), op.err, &s_abort);
         ok = ok && (k < 2 || mbar_wait(&bar_epi[t], (uint32_t)(((k - 2) >> 1) & 1), op.err, &s_abort));
         if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        // products kept by the split: H1 Z2 first (it frees the lo tiles), then
-        // H1 Z1 + H2 Z1 (+ H3 Z1) with the hi tiles
+        // products kept by the split: H1 Z1 + H2 Z1 (+ H3 Z1) with the hi tiles first
+        // (committed to bar_hi, which frees them for the next item), then H1 Z2 once
+        // the lo tiles are written
         const uint32_t dcol = tmem + (uint32_t)t * 256u;
         for (int grp = 0; grp < 2; ++grp) {
-          const int zk = grp == 0 ? 1 : 0;                 // Z piece of this group
-          const int j_hi = grp == 0 ? 1 : nh;               // H pieces of this group
+          if (grp == 1) {
+            if (!mbar_wait(&bar_ready_lo[t], (uint32_t)((k >> 1) & 1), op.err, &s_abort)) break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const int zk = grp;                                // Z piece of this group: 0 hi, 1 lo
+          const int j_hi = grp == 0 ? nh : 1;               // H pieces of this group
           for (int j = 0; j < j_hi; ++j) {
             const uint32_t ha = hh + (uint32_t)j * kHTile, zb = zz[zk];
             for (int kk = 0; kk < 8; ++kk) {
@@ -361,12 +372,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
               }
             }
           }
-          if (grp == 0)
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&bar_lo[t])));
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(grp == 0 ? &bar_hi[t] : &bar_mma[t])));
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_u32(&bar_mma[t])));
+        if (*(volatile int *)&s_abort) break;
         mbar_arrive(&bar_full[t]);
       }
       // drain: the last item's MMAs must complete before the tiles and tensor memory go away
