@@ -93,7 +93,7 @@ def algorithmic_costs(model, d, nado, ado_table, nb_counts, prec):
 # Measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per work item
 # (one ADO of one branch) of one RK4 stage of the tensor-core path, from the ncu
 # capture summarised in profiles/tc_stage_c3.md (4-branch case, scaled per item).
-TC_STAGE_TRAFFIC_BYTES_PER_ITEM = 752.9e3
+TC_STAGE_TRAFFIC_BYTES_PER_ITEM = 753.4e3
 
 
 class ClockSampler:
