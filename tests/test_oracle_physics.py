@@ -13,6 +13,8 @@
   * P6 harmonic 2D: the third-order response of a linearly coupled harmonic
     oscillator with a linear dipole vanishes (nested commutators of linear
     operators are c-numbers).
+  * P7 truncation: the c1 spectrum converges monotonically in the hierarchy depth
+    and in the number of Pade terms.
 """
 import math
 
@@ -156,3 +158,26 @@ def test_harmonic_third_order_vanishes():
     rho_eq, _, _ = Hm.equilibrate(pm, g["dt_fs"], t_eq_fs=g["t_eq_fs"])
     RIm, _ = Hm.response_2d(pm, rho_eq, g)
     assert np.max(np.abs(RIm)) > 1e-2 * np.max(np.abs(R1)) ** 2
+
+
+def _c1_spectrum(depth_L, K_pade, grid):
+    model, _ = W.config("c1")
+    model["modes"][0]["K_pade"] = K_pade
+    model["depth_L"] = depth_L
+    return Hm.spectrum_2d(M.Problem(model), grid)[3]
+
+
+def test_depth_and_pade_convergence():
+    """P7: on the c1 model the spectrum converges monotonically in the hierarchy
+    depth L and in the number of Pade terms K (successive changes shrink)."""
+    grid = W.grid(0.5, 8, 12, 12, (0.0,), t_eq_fs=50.0)
+    S = [_c1_spectrum(L, 1, grid) for L in range(1, 7)]
+    dL = [np.abs(S[i + 1] - S[i]).max() / np.abs(S[i + 1]).max() for i in range(5)]
+    assert all(dL[i + 1] < dL[i] for i in range(4)), dL
+    assert dL[-1] < 1e-3
+    # dt = 0.25 fs keeps dt x (L x the largest Pade rate) inside the RK4 region for K <= 4
+    grid = W.grid(0.25, 16, 12, 12, (0.0,), t_eq_fs=50.0)
+    S = [_c1_spectrum(3, K, grid) for K in range(1, 5)]
+    dK = [np.abs(S[i + 1] - S[i]).max() / np.abs(S[i + 1]).max() for i in range(3)]
+    assert all(dK[i + 1] < 0.2 * dK[i] for i in range(2)), dK
+    assert dK[-1] < 1e-5
