@@ -287,6 +287,19 @@ static void rk4_steps(heom_hier *h, typename CxT<R>::type *y, typename CxT<R>::t
     if (precision == HEOM_TC) {
       if (!tc_supported(h->tc)) throw Fail{HEOM_EINVAL, "tensor-core path not prepared for this hierarchy"};
       tc_rk4_steps(h->tc, fy, fa, fb, branches, dt, nsteps, st);
+    } else if (h->M.d >= kVbTiledMinD) {
+      // larger bases: the commutator tiled through shared memory, one block per
+      // 32 x 32 output tile of one item
+      const int tiles = (h->M.d + 31) / 32;
+      const int64_t nb = (int64_t)branches * h->M.n_ado * tiles * tiles;
+      if (nb > 0x7fffffffLL) throw Fail{HEOM_EINVAL, "too many tiles for one launch"};
+      for (int64_t s = 0; s < nsteps; ++s) {
+        stage_kernel_vb_tiled<<<(unsigned)nb, 256, 0, st>>>(fy, fy, fa, (float)(dt / 4), h->vb, tiles);
+        stage_kernel_vb_tiled<<<(unsigned)nb, 256, 0, st>>>(fa, fy, fb, (float)(dt / 3), h->vb, tiles);
+        stage_kernel_vb_tiled<<<(unsigned)nb, 256, 0, st>>>(fb, fy, fa, (float)(dt / 2), h->vb, tiles);
+        stage_kernel_vb_tiled<<<(unsigned)nb, 256, 0, st>>>(fa, fy, fy, (float)dt, h->vb, tiles);
+        count_launch(4);
+      }
     } else {
       const auto sh = tuned_shape(h, kTuneStageVb, total, st, [&](int block, int grid) {
         stage_kernel_vb<<<grid, block, 0, st>>>(fy, fy, fa, (float)(dt / 4), h->vb, total);

@@ -86,6 +86,82 @@ __global__ void __launch_bounds__(256) stage_kernel_vb(const float2 *__restrict_
   }
 }
 
+// Tiled variant for larger bases: one block per 32 x 32 output tile of one item,
+// 8 rows x 32 columns of threads with 4 rows each.  The commutator's contraction
+// runs over 32-wide slices of H' and w_n staged in shared memory (each element
+// reused 32 times instead of re-read per output); the decay and system-bath terms
+// are the same elementwise code as stage_kernel_vb, in the same summation order.
+__global__ void __launch_bounds__(256) stage_kernel_vb_tiled(const float2 *__restrict__ w, const float2 *y,
+                                                             float2 *out, float alpha, VbModel M, int tiles) {
+  __shared__ float sHa[32][33], sHb[32][33];
+  __shared__ float2 sWa[32][33], sWb[32][33];
+  const int d = M.d;
+  const int64_t dd = (int64_t)d * d;
+  const int64_t item = blockIdx.x / (tiles * tiles);
+  const int tile = (int)(blockIdx.x - item * tiles * tiles);
+  const int a0 = (tile / tiles) * 32, b0 = (tile % tiles) * 32;
+  const int n = (int)(item % M.n_ado);
+  const int64_t br = item / M.n_ado;
+  const float2 *wb = w + br * M.n_ado * dd;
+  const float2 *wn = wb + (int64_t)n * dd;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float re[4] = {0.f, 0.f, 0.f, 0.f}, im[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int c0 = 0; c0 < d; c0 += 32) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = ty + 8 * i;                       // tile row / slice index
+      const bool ca = c0 + tx < d, cr = c0 + r < d;
+      sHa[r][tx] = (a0 + r < d && ca) ? M.H[(int64_t)(a0 + r) * d + c0 + tx] : 0.f;
+      sWa[r][tx] = (a0 + r < d && ca) ? wn[(int64_t)(a0 + r) * d + c0 + tx] : make_float2(0.f, 0.f);
+      sHb[r][tx] = (cr && b0 + tx < d) ? M.H[(int64_t)(c0 + r) * d + b0 + tx] : 0.f;
+      sWb[r][tx] = (cr && b0 + tx < d) ? wn[(int64_t)(c0 + r) * d + b0 + tx] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float2 x = sWb[k][tx];
+      const float h2 = sHb[k][tx];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = ty + 8 * i;
+        const float h1 = sHa[r][k];
+        const float2 z = sWa[r][k];
+        re[i] += h1 * x.x - z.x * h2;
+        im[i] += h1 * x.y - z.y * h2;
+      }
+    }
+    __syncthreads();
+  }
+  const int b = b0 + tx;
+  if (b >= d) return;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int a = a0 + ty + 8 * i;
+    if (a >= d) continue;
+    const int64_t el = (int64_t)a * d + b;
+    float ore = im[i], oim = -re[i];
+    const float dec = (float)M.decay[n];
+    const float2 self = wn[el];
+    ore -= dec * self.x;
+    oim -= dec * self.y;
+    for (int s = 0; s < M.n_modes; ++s) {
+      const int o0 = M.nb_off[n * M.n_modes + s], o1 = M.nb_off[n * M.n_modes + s + 1];
+      if (o0 == o1) continue;
+      const float la = M.lam[s * d + a], lb = M.lam[s * d + b];
+      const float f = la - lb, g = la + lb;
+      for (int q = o0; q < o1; ++q) {
+        const float2 xv = wb[(int64_t)M.nb_idx[q] * dd + el];
+        const float p = M.nb_cB[q] * g, qq = M.nb_cA[q] * f;
+        ore += p * xv.x + qq * xv.y;
+        oim += p * xv.y - qq * xv.x;
+      }
+    }
+    const int64_t e = item * dd + el;
+    const float2 yv = y[e];
+    out[e] = make_float2(yv.x + alpha * ore, yv.y + alpha * oim);
+  }
+}
+
 __global__ void convert_f64_to_f32(const double2 *__restrict__ x, float2 *__restrict__ y, int64_t n) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     y[i] = make_float2((float)x[i].x, (float)x[i].y);

@@ -276,6 +276,12 @@ struct VbModel {
 // kappa = -i cA (lam_a - lam_b) + cB (lam_a + lam_b) for the coupling list of (n, s).
 __global__ void __launch_bounds__(256) stage_kernel_vb(const float2 *__restrict__ w, const float2 *y, float2 *out,
                                                        float alpha, VbModel M, int64_t total);
+// The same stage with the commutator tiled through shared memory (one block per
+// 32 x 32 output tile of one item; grid = items x tiles^2, tiles = ceil(d / 32)).
+// out may alias y but not w.
+constexpr int kVbTiledMinD = 24;
+__global__ void __launch_bounds__(256) stage_kernel_vb_tiled(const float2 *__restrict__ w, const float2 *y,
+                                                             float2 *out, float alpha, VbModel M, int tiles);
 
 // Similarity transform of every ADO: out_n = P^T x_n P (double accumulation).
 // Two passes through tmp (double2, same element count as x).
