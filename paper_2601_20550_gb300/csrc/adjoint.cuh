@@ -23,7 +23,7 @@ constexpr int kAdjMaxExp = 32;
 constexpr int kAdjMaxVl = 4 * 16 * 16;   // sum_s n_s^2 (n_s <= 16)
 
 // y += a x over n complex entries.
-__global__ void __launch_bounds__(256) axpy_kernel(double2 *__restrict__ y, const double2 *__restrict__ x, double a,
+static __global__ void __launch_bounds__(256) axpy_kernel(double2 *__restrict__ y, const double2 *__restrict__ x, double a,
                                                    int64_t n) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = x[e];
@@ -34,7 +34,7 @@ __global__ void __launch_bounds__(256) axpy_kernel(double2 *__restrict__ y, cons
 
 // out_n = -(in_n)^dagger for every ADO matrix (the map that turns the R_I trunk
 // into the R_II trunk; as a real-linear map it is its own adjoint).
-__global__ void __launch_bounds__(256) neg_dagger_kernel(const double2 *__restrict__ in, double2 *__restrict__ out,
+static __global__ void __launch_bounds__(256) neg_dagger_kernel(const double2 *__restrict__ in, double2 *__restrict__ out,
                                                          int d, int64_t total) {
   const int64_t dd = (int64_t)d * d;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(256) comm_grad_kernel(const double2 *__restric
 // constants).  One block per item; warps walk rows for the V X^L part (mode
 // digit of the row uniform per warp) and columns for the X^R V part.
 // entry_exp[q] = exponential j of a down-neighbour entry, -1 for up entries.
-__global__ void __launch_bounds__(256) coupling_grad_kernel(const double2 *__restrict__ g,
+static __global__ void __launch_bounds__(256) coupling_grad_kernel(const double2 *__restrict__ g,
                                                             const double2 *__restrict__ w, DevModel<double> M,
                                                             const int *__restrict__ ado, int n_exp,
                                                             const int *__restrict__ entry_exp, int64_t n_items,
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(256) coupling_grad_kernel(const double2 *__res
 
 // Trace adjoint: R_b = c tr{mu rho_{b,0}} for every branch b, c = i^order.
 // lam_{b,0} += conj(c) Rbar_b mu^T, and Gmu[p][q] += Re(conj(Rbar_b) c rho_{b,0}[q][p]).
-__global__ void __launch_bounds__(256) trace_adjoint_kernel(double2 *__restrict__ lam, const double2 *__restrict__ rho,
+static __global__ void __launch_bounds__(256) trace_adjoint_kernel(double2 *__restrict__ lam, const double2 *__restrict__ rho,
                                                             const double2 *__restrict__ rbar, int64_t rbar_stride,
                                                             const double *__restrict__ mu, int d, int64_t per_branch,
                                                             int branches, double c_re, double c_im,

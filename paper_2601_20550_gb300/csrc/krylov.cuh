@@ -13,7 +13,7 @@ namespace heom {
 constexpr int kKrylovBlocks = 512;
 
 // partial[blk * k + j] = sum over this block's slice of conj(V_j[e]) w[e], j < k.
-__global__ void __launch_bounds__(256) multi_dot_kernel(const double2 *__restrict__ V, int64_t n, int k,
+static __global__ void __launch_bounds__(256) multi_dot_kernel(const double2 *__restrict__ V, int64_t n, int k,
                                                         const double2 *__restrict__ w, double2 *__restrict__ partial) {
   __shared__ double sre[256], sim[256];
   for (int j = 0; j < k; ++j) {
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) multi_dot_kernel(const double2 *__restric
 }
 
 // w += sum_{j < k} c_j V_j (complex coefficients c on the device).
-__global__ void __launch_bounds__(256) multi_axpy_kernel(double2 *__restrict__ w, const double2 *__restrict__ V,
+static __global__ void __launch_bounds__(256) multi_axpy_kernel(double2 *__restrict__ w, const double2 *__restrict__ V,
                                                          int64_t n, int k, const double2 *__restrict__ c) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     double2 acc = w[e];
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) multi_axpy_kernel(double2 *__restrict__ w
 }
 
 // x = a x (complex a).
-__global__ void __launch_bounds__(256) zscal_kernel(double2 *__restrict__ x, int64_t n, double ar, double ai) {
+static __global__ void __launch_bounds__(256) zscal_kernel(double2 *__restrict__ x, int64_t n, double ar, double ai) {
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
     const double2 v = x[e];
     x[e] = make_double2(ar * v.x - ai * v.y, ar * v.y + ai * v.x);
