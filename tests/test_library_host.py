@@ -90,3 +90,23 @@ def test_invalid_descriptors_rejected(mutate):
     with pytest.raises(H.HeomError) as ei:
         H.heom_build_hierarchy(model)
     assert ei.value.status == -1
+
+
+def test_new_entry_points_reject_bad_arguments_on_host():
+    """Argument checks that run before any device work (no GPU needed)."""
+    import ctypes as ct
+    L = H.lib()
+    h = H.heom_build_hierarchy(W.small_two_mode())
+    out = ct.c_void_p()
+    its = ct.c_int(0)
+    # steady state: tol, restart, max_iter and steps_per_matvec are validated first
+    for tol, restart, max_iter, k in ((0.0, 30, 10, 0), (1e-10, 1, 10, 0), (1e-10, 30, 0, 0), (1e-10, 30, 10, -1)):
+        rc = L.heom_steady_state(h.h, tol, restart, max_iter, 0.5, k, ct.byref(out), ct.byref(its))
+        assert rc == -1 and not out.value
+    # batched and gradient entry points: null arguments
+    g = H.marshal_grid(W.grid(0.5, 2, 3, 3, (0.0,)))
+    assert L.heom_response_2d_batched(None, None, 1, ct.byref(g), None, None, None) == -1
+    assert L.heom_response_2d_grad(h.h, None, ct.byref(g), None, 64, None, None) == -1
+    # a hierarchy that has not propagated has no tuned launch shapes
+    assert H.heom_get_tuning(h) == []
+    assert L.heom_get_tuning(None, 0, None, None, None, None) == 0
