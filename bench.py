@@ -196,12 +196,22 @@ def run_reference(args, cfg, rank, world):
             vals.append(r)
     value = float(np.mean([v["value"] for v in vals]))
     model, grid = W.config(cfg)
+    # the native arm's config for the same workload (the oracle times a bounded sample of it)
+    from oracle import model as OM
+    prob = OM.Problem(model)
+    prec = WORKLOADS[args.workload][1]
+    conf = describe(cfg, model, grid, prob.d, prob.nado)
+    B = 2 * grid["n1"]
+    conf.update({"parallelism": "replicas" if world > 1 else "single-gpu",
+                 "l2": "inputs larger than L2 (state %.1f GB)"
+                       % (B * prob.nado * prob.d ** 2 * (16 if prec == 0 else 8) / 1e9),
+                 "precision": PREC_NAME[prec]})
     line = {"impl": "reference", "metric": "HEOM ADO-updates/s (2D spectra/hour derived)",
             "value": value, "unit": "ADO-updates/s", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean([v["seconds"] for v in vals])),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded water-like MAB model)",
-            "config": {"workload": cfg + " (oracle sample: one branch)"},
+            "config": conf,
             "cpu_baseline": {"value": value, "unit": "ADO-updates/s", "cores": os.cpu_count(),
                              "kind": "oracle", "sample": vals[0]["sample"]},
             "e2e": {"value": value, "unit": "ADO-updates/s", "h2d_bytes_per_step": 0,
