@@ -68,7 +68,7 @@ def rows_ado_updates(grid, nado, j0, j1):
 
 
 # ---------------------------------------------------------------------------
-# Algorithmic cost per ADO-update of the fused stage kernel (see DESIGN.md)
+# Algorithmic cost per ADO-update of the fused stage kernel
 # ---------------------------------------------------------------------------
 def algorithmic_costs(model, d, nado, ado_table, nb_counts, prec):
     """Algorithmic flops and bytes of one ADO-update (one ADO advanced by one RK4 step).
