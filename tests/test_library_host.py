@@ -110,3 +110,19 @@ def test_new_entry_points_reject_bad_arguments_on_host():
     # a hierarchy that has not propagated has no tuned launch shapes
     assert H.heom_get_tuning(h) == []
     assert L.heom_get_tuning(None, 0, None, None, None, None) == 0
+
+
+def test_c5_batch_sets_are_seeded_and_uneven():
+    a, b = W.c5_batch(), W.c5_batch()
+    assert a == b and len(a) == 16
+    dims = {tuple(md["n_levels"] for md in m["modes"]) for m in a}
+    assert len(dims) > 4 and all(set(x) <= {4, 5, 6} for x in dims)
+    base, _ = W.config("c5")
+    for m in a:
+        for md, md0 in zip(m["modes"], base["modes"]):
+            assert abs(md["gamma_cm"] / md0["gamma_cm"] - 1) <= 0.05
+    # the library builds the smallest set's hierarchy on the host
+    small = min(a, key=lambda m: np.prod([md["n_levels"] for md in m["modes"]]))
+    small = dict(small, depth_L=2)
+    h = H.heom_build_hierarchy(small)
+    assert h.d == int(np.prod([md["n_levels"] for md in small["modes"]]))

@@ -140,6 +140,27 @@ def c5():
             grid(0.25, 16, 256, 256, (0.0, 50.0, 200.0), t_eq_fs=200.0))
 
 
+def c5_batch(n_sets=16, seed=2605):
+    """The c5 batch of parameter sets with uneven basis sizes: per set, every mode
+    gets n_s levels drawn from {4, 5, 6}, and its anharmonicity, V_SL and gamma and
+    each pair's cubic couplings a factor 1 + 0.05 U(-1, 1) (seeded).  Returns a
+    list of model dicts (the grid is c5's)."""
+    rng = np.random.default_rng(seed)
+    base, _ = c5()
+    out = []
+    for _ in range(n_sets):
+        m = copy.deepcopy(base)
+        for md in m["modes"]:
+            md["n_levels"] = int(rng.choice([4, 5, 6]))
+            for key in ("morse_D_cm", "V_SL", "gamma_cm"):
+                md[key] = float(md[key] * (1 + 0.05 * rng.uniform(-1, 1)))
+        for pr in m["pairs"]:
+            for key in ("g_s2t_cm", "g_st2_cm"):
+                pr[key] = float(pr[key] * (1 + 0.05 * rng.uniform(-1, 1)))
+        out.append(m)
+    return out
+
+
 CONFIGS = {"c1": c1, "c2": c2, "c3": c3, "c4": c4, "c5": c5}
 
 
