@@ -13,6 +13,10 @@ Pins (tests/test_oracle_model.py):
     Bernoulli series to order 2N; convergence to the Matsubara values 2*pi*k.
   * Bath coefficients: the Drude correlation function by direct quadrature.
   * Hierarchy size C(L+D, D) and neighbour consistency by brute force.
+  * System (tests/test_oracle_couplings.py): V_s and the counter term Lambda <V_s^2>
+    for V_SL != 0 against ladder-operator matrix elements (V^2 squared in a larger
+    basis); the square-linear pure-dephasing closed form; the quadratic and
+    cross-mode dipole terms through the zero-bath linear response.
 """
 import itertools
 import math
