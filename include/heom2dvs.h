@@ -329,7 +329,9 @@ heom_status heom_trace_dev(heom_hier *h, const void *state, int branches, int pr
  * synchronise the device, a plug-in has buffers but no allocation rights).
  * The paper has no counterpart: it is a deployment variant of the RK4 step.
  *   state    device pointer, [branches][n_ado][d][d] complex128 (HEOM_FP64
- *            layout), advanced in place by n_steps RK4 steps on `stream`.
+ *            layout), advanced in place by n_steps RK4 steps on `stream`;
+ *            16-byte aligned, and dt_fs finite and > 0 (HEOM_EINVAL otherwise,
+ *            before any device work).
  * The two RK4 scratch buffers are a file-scope __device__ array of
  * 2 x HEOM_NOALLOC_MAX_BYTES that every GPU loading the library holds until the
  * process exits; states larger than HEOM_NOALLOC_MAX_BYTES are rejected with

@@ -126,3 +126,17 @@ def test_c5_batch_sets_are_seeded_and_uneven():
     small = dict(small, depth_L=2)
     h = H.heom_build_hierarchy(small)
     assert h.d == int(np.prod([md["n_levels"] for md in small["modes"]]))
+
+
+def test_noalloc_rejects_bad_pointers_before_any_launch():
+    """heom_propagate_noalloc checks its arguments before it touches the device:
+    a state pointer that is not 16-byte aligned (complex128) and a non-finite dt
+    are rejected with HEOM_EINVAL (no GPU needed; the pointers are never used)."""
+    import ctypes as ct
+    L = H.lib()
+    h = H.heom_build_hierarchy(W.small_two_mode())
+    rc = L.heom_propagate_noalloc(h.h, ct.c_void_p(0x10008), 1, 0.5, 1, None)
+    assert rc == -1 and "aligned" in H.heom_last_error()
+    for dt in (float("inf"), float("nan"), 0.0, -0.5):
+        rc = L.heom_propagate_noalloc(h.h, ct.c_void_p(0x10000), 1, dt, 1, None)
+        assert rc == -1 and "bad arguments" in H.heom_last_error()
