@@ -55,13 +55,17 @@ __device__ __forceinline__ void stage_element(const typename CxT<R>::type *__res
   const C *wn = wb + (int64_t)n * dd;
   R re = 0, im = 0;
   const R *Ha = M.H + (int64_t)a * d;
+  // Each product is its own fused multiply-add into the running sum (one FP64
+  // pipe operation per multiply-add; the grouped form h1 x - z h2 costs three).
   for (int c = 0; c < d; ++c) {
     const R h1 = Ha[c];
     const R h2 = M.H[(int64_t)c * d + b];
     const C x = wn[(int64_t)c * d + b];
     const C z = wn[(int64_t)a * d + c];
-    re += h1 * x.x - z.x * h2;
-    im += h1 * x.y - z.y * h2;
+    re = fma(h1, x.x, re);
+    im = fma(h1, x.y, im);
+    re = fma(-z.x, h2, re);
+    im = fma(-z.y, h2, im);
   }
   // -i [H, w]
   R ore = im, oim = -re;
