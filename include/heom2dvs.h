@@ -186,7 +186,9 @@ heom_status heom_trace(heom_hier *h, const heom_state *rho, int order, double *o
  *   (Omega1 index q, Omega3 index p), Omega_p = 2 pi p / (N m dt), with the
  *   trapezoid weights 1/2 at t = 0 and S_C(q, p) = S_R((n1 - q) mod n1, p) + S_NR(q, p).
  * rho_eq must be a single-branch FP64 state (from heom_equilibrate).  The
- * propagation runs in the hierarchy's precision; traces accumulate in FP64.
+ * propagation runs in the hierarchy's precision (with HEOM_TC, the
+ * single-branch t1 trunk runs on the FP32 CUDA-core stage and every batched
+ * propagation on the tensor cores); traces accumulate in FP64.
  */
 heom_status heom_response_2d(heom_hier *h, const heom_state *rho_eq, const heom_grid *g,
                              double *R_I, double *R_II, double *S_C);
@@ -346,6 +348,52 @@ heom_status heom_trace_dev(heom_hier *h, const void *state, int branches, int pr
 #define HEOM_NOALLOC_MAX_BYTES (16LL * 1024 * 1024)
 heom_status heom_propagate_noalloc(heom_hier *h, void *state, int branches, double dt_fs,
                                    int64_t n_steps, void *stream);
+
+/*
+ * Checkpoint files (no counterpart in the paper: resume support for runs of
+ * hours, e.g. the c5 scan).  A file holds a header (magic "HEOMCKPT", format
+ * version, payload size, a tag), the payload and a CRC-32 (IEEE 802.3) of
+ * header and payload; it is written under a temporary name and renamed, so an
+ * interrupted write leaves the previous file intact.
+ *   heom_ckpt_write   host buffer [bytes] -> file
+ *   heom_ckpt_read    file -> host buffer [bytes]; the buffer changes only if the
+ *                     whole file passes its check
+ *   heom_ckpt_verify  integrity check only; *payload_bytes (may be NULL) receives
+ *                     the payload size
+ *   heom_state_save   a state's device storage as held (complex128 product basis
+ *                     or complex64 coupling basis) with its shape in the tag
+ *   heom_state_load   into a state of the same shape and precision, bit for bit;
+ *                     the state changes only if the file passes its check
+ * Errors: HEOM_ECKPT (missing, truncated, foreign or corrupted file: magic,
+ * version or CRC mismatch), HEOM_EINVAL (payload size or state shape differs
+ * from the caller's), HEOM_ECUDA (device copies).
+ */
+heom_status heom_ckpt_write(const char *path, const void *host, uint64_t bytes);
+heom_status heom_ckpt_read(const char *path, void *host, uint64_t bytes);
+heom_status heom_ckpt_verify(const char *path, uint64_t *payload_bytes);
+heom_status heom_state_save(const heom_state *s, const char *path);
+heom_status heom_state_load(heom_state *s, const char *path);
+
+/*
+ * Time limit of every device-side wait of this hierarchy's tensor-core stage
+ * kernel (mbarrier waits between its producer, MMA-issue and epilogue warps;
+ * no counterpart in the paper: a watchdog of the persistent kernel).  Default
+ * 2 s.  A wait that runs out raises the hierarchy's device error word, the
+ * kernel drains the tensor-core work it has committed, frees its tensor memory
+ * and returns, and the calling entry point returns HEOM_ETIMEOUT (the CUDA
+ * context stays usable; the state of that call is not valid).  ns must be > 0
+ * (HEOM_EINVAL).
+ */
+heom_status heom_set_wait_limit_ns(heom_hier *h, uint64_t ns);
+
+/*
+ * Host-side allocation-failure injection for tests of the error paths (no
+ * counterpart in the paper): after `after` more device allocations by the
+ * library succeed, every following one fails as if the device were out of
+ * memory, and the entry point that needed it returns HEOM_ENOMEM.  after < 0
+ * switches the injection off (the default).  Process-wide.
+ */
+void heom_debug_fail_alloc(int64_t after);
 
 void heom_free_hier(heom_hier *h);
 void heom_free_state(heom_state *s);

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libheom2dvs.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["model.cpp", "kernels.cu", "api.cu", "batched.cu", "grad.cu", "steady.cu", "tc_stage.cu", "noalloc.cu"]
+SOURCES = ["model.cpp", "kernels.cu", "api.cu", "batched.cu", "grad.cu", "steady.cu", "tc_stage.cu", "noalloc.cu", "checkpoint.cu"]
 
 
 def nvcc():

@@ -33,6 +33,22 @@ static std::atomic<uint64_t> g_launches{0};
 
 void count_launch(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+// Allocation-failure injection: -1 = off; otherwise the number of device
+// allocations that still succeed before every following one fails.
+static std::atomic<int64_t> g_alloc_budget{-1};
+
+cudaError_t device_malloc(void **p, size_t bytes) {
+  int64_t b = g_alloc_budget.load();
+  while (b >= 0) {
+    if (b == 0) {
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
+    if (g_alloc_budget.compare_exchange_weak(b, b - 1)) break;
+  }
+  return cudaMalloc(p, bytes);
+}
+
 }  // namespace heom
 
 using namespace heom;
@@ -281,11 +297,15 @@ void response_2d_rows_impl(heom_hier *h, const heom_state *eq, const heom_grid *
     const int nj = std::min(jc, n1 - j0);
     const int B = 2 * nj;
     C *BR = (C *)P0.p;
-    // trunk: rephasing first kick, propagated to t1 = j0 m dt
+    // trunk: rephasing first kick, propagated to t1 = j0 m dt.  On the tensor-core
+    // path the single-branch trunk runs on the FP32 CUDA-core stage (same
+    // coupling-basis complex64 state): its error would reach every t1 row, and one
+    // branch is a small share of the scan's work.
+    const int trunk_prec = M.precision == HEOM_TC ? HEOM_FP32 : M.precision;
     kick_into<R>(h, (const C *)eqR.p, (C *)T.p, 1, 2, st);
-    rk4_steps<R>(h, (C *)T.p, (C *)ta.p, (C *)tb.p, 1, dt, (int64_t)(jr0 + j0) * m, st, M.precision);
+    rk4_steps<R>(h, (C *)T.p, (C *)ta.p, (C *)tb.p, 1, dt, (int64_t)(jr0 + j0) * m, st, trunk_prec);
     for (int j = 0; j < nj; ++j) {
-      if (j > 0) rk4_steps<R>(h, (C *)T.p, (C *)ta.p, (C *)tb.p, 1, dt, m, st, M.precision);
+      if (j > 0) rk4_steps<R>(h, (C *)T.p, (C *)ta.p, (C *)tb.p, 1, dt, m, st, trunk_prec);
       kick2_pair_kernel<R><<<grid_for(per_branch), 256, 0, st>>>(
           (const C *)T.p, BR + (int64_t)j * per_branch, BR + (int64_t)(nj + j) * per_branch,
           mu_of<R>(h, 1), mu_of<R>(h, 2), M.d, per_branch);
@@ -331,7 +351,9 @@ template void response_2d_rows_impl<float>(heom_hier *, const heom_state *, cons
 void ensure_device(heom_hier *h) {
   if (h->on_device) return;
   Model &M = h->M;
-  CUDA_TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  // (a set-up that failed part-way is redone from the start by the next call;
+  // what it allocated stays owned by the handle)
+  if (!h->stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
   std::vector<double> vl;
   DevModel<double> d64{};
   d64.d = M.d;
@@ -539,8 +561,8 @@ heom_status heom_propagate(heom_hier *h, heom_state *rho, double dt_fs, int64_t 
   if (!h || !rho || n_steps < 0) return fail(HEOM_EINVAL, "bad propagate arguments");
   if (rho->d != h->M.d || rho->n_ado != h->M.n_ado) return fail(HEOM_EINVAL, "state does not match hierarchy");
   return guarded([&]() -> heom_status {
-    ensure_device(h);
     stability_check(h, dt_fs);
+    ensure_device(h);
     const size_t bytes = rho->elems() * rho->elem_bytes();
     DeviceBuffer a(bytes), b(bytes);
     if (rho->precision == HEOM_FP64)
@@ -560,8 +582,8 @@ heom_status heom_propagate_dev(heom_hier *h, void *state, void *scratch_a, void 
   if ((((uintptr_t)state | (uintptr_t)scratch_a | (uintptr_t)scratch_b) & (precision == HEOM_FP64 ? 15u : 7u)))
     return fail(HEOM_EINVAL, "state buffers must be aligned to their complex element size");
   return guarded([&]() -> heom_status {
-    ensure_device(h);
     stability_check(h, dt_fs);
+    ensure_device(h);
     cudaStream_t st = (cudaStream_t)stream;
     if (precision == HEOM_FP64)
       rk4_steps<double>(h, (double2 *)state, (double2 *)scratch_a, (double2 *)scratch_b, branches, dt_fs, n_steps, st, precision);
@@ -607,6 +629,7 @@ heom_status heom_equilibrate(heom_hier *h, double dt_fs, double t_max_fs, double
   *rho_eq = nullptr;
   {
     heom_status e = guarded([&]() -> heom_status {
+      stability_check(h, dt_fs);
       ensure_device(h);
       return HEOM_OK;
     });
@@ -861,6 +884,14 @@ heom_status heom_response_1d(heom_hier *h, const heom_state *rho_eq, double dt_f
     return HEOM_OK;
   });
 }
+
+heom_status heom_set_wait_limit_ns(heom_hier *h, uint64_t ns) {
+  if (!h || ns == 0) return fail(HEOM_EINVAL, "bad wait limit arguments");
+  h->tc.wait_ns = ns;
+  return HEOM_OK;
+}
+
+void heom_debug_fail_alloc(int64_t after) { g_alloc_budget.store(after < 0 ? -1 : after); }
 
 void heom_free_hier(heom_hier *h) { delete h; }
 void heom_free_state(heom_state *s) { delete s; }

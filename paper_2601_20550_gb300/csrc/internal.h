@@ -49,7 +49,7 @@ template <typename T>
 T *dev_upload(const std::vector<T> &v) {
   T *p = nullptr;
   size_t bytes = std::max<size_t>(1, v.size() * sizeof(T));
-  if (cudaMalloc(&p, bytes) != cudaSuccess) throw Fail{HEOM_ENOMEM, "cudaMalloc failed (model tables)"};
+  if (device_malloc((void **)&p, bytes) != cudaSuccess) throw Fail{HEOM_ENOMEM, "device allocation failed (model tables)"};
   if (!v.empty()) CUDA_TRY(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
   return p;
 }
@@ -67,10 +67,10 @@ struct DeviceBuffer {
   void alloc(size_t n) {
     release();
     if (n == 0) n = 16;
-    if (cudaMalloc(&p, n) != cudaSuccess) {
+    if (device_malloc(&p, n) != cudaSuccess) {
       p = nullptr;
       cudaGetLastError();
-      throw Fail{HEOM_ENOMEM, "cudaMalloc of " + std::to_string(n) + " bytes failed"};
+      throw Fail{HEOM_ENOMEM, "device allocation of " + std::to_string(n) + " bytes failed"};
     }
     bytes = n;
   }
@@ -157,6 +157,8 @@ heom_status guarded(F &&f) {
     return fail(e.st, e.msg);
   } catch (const std::invalid_argument &e) {
     return fail(HEOM_EINVAL, e.what());
+  } catch (const DeviceOom &e) {
+    return fail(HEOM_ENOMEM, e.what());
   } catch (const std::bad_alloc &) {
     return fail(HEOM_ENOMEM, "host allocation failed");
   } catch (const std::exception &e) {

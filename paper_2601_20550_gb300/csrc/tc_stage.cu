@@ -11,9 +11,8 @@
 //   2. one thread of warp 16 issues tcgen05.mma: D = Z^T H' - H' Z^T = [H', Z]^T
 //      with the H' pieces (hi, mid, lo) resident in shared memory and FP32
 //      accumulation in tensor memory (256 columns: Re D | Im D, double-buffered),
-//      in two commit groups: the products with the hi tiles as soon as those are
-//      written (their completion frees the hi tiles for the next item), then the
-//      product with the lo tiles;
+//      the small split products first and the hi x hi product last (see the
+//      issue loop for why), the tiles released when all have completed;
 //   3. epilogue warps 12-15 read D from tensor memory (lane = column b of w_n,
 //      column = row a) and store tpart = alpha (-i C) with coalesced accesses.
 // vterm_kernel then adds y, tpart and the elementwise decay and system-bath
@@ -48,7 +47,13 @@ constexpr int kEpilogue = 128;                   // warps 12-15
 constexpr int kMmaWarp = 16;                     // warp 16: tensor-core issue
 constexpr int kProdRows = 12;                    // rows per producer batch (2 batches cover 144 >= 128 rows)
 static_assert(kProducers + kEpilogue + 32 == kThreads, "warp roles");
-constexpr long kWaitLimit = 1L << 26;
+// Bounded waits: a wait gives up after the hierarchy's time limit (globaltimer,
+// checked at the second poll and then every 256 polls) or after kWaitPolls
+// polls, whichever comes first.
+constexpr long kWaitPolls = 1L << 30;
+// Drain of the MMAs already committed when a block aborts: bounded by its own
+// limit, independent of the (possibly shortened) wait limit.
+constexpr uint64_t kDrainNs = 2000000000ull;
 
 struct TcArgs {
   const float2 *w;
@@ -128,18 +133,57 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 
 // Bounded wait on an mbarrier phase; returns false (and raises the error word)
 // when the iteration limit runs out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int *abort_flag) {
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// A wait also returns false, without raising the error word, as soon as another
+// role of the block has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int *abort_flag,
+                                          uint64_t limit_ns) {
   const uint32_t addr = smem_u32(bar);
-  for (long it = 0; it < kWaitLimit; ++it) {
+  if (mbar_try(addr, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (long it = 1; it < kWaitPolls; ++it) {
     if (mbar_try(addr, parity)) return true;
-    if ((it & 1023) == 1023 && *(volatile int *)abort_flag) return false;
+    if (it == 1 || (it & 255) == 0) {
+      if (*(volatile int *)abort_flag) return false;
+      if (global_ns() - t0 > limit_ns) break;
+    }
   }
   atomicExch(err, 1);
   *(volatile int *)abort_flag = 1;
   return false;
 }
 
-__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kProducers)); }
+// Wait for the completion of MMAs that were committed before an abort; the
+// abort flag does not end this wait (the tensor memory and the tiles they use
+// must outlive them).  Bounded by kDrainNs.
+__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity, int *err) {
+  const uint32_t addr = smem_u32(bar);
+  const uint64_t t0 = global_ns();
+  for (long it = 0; it < kWaitPolls; ++it) {
+    if (mbar_try(addr, parity)) return;
+    if ((it & 255) == 255 && global_ns() - t0 > kDrainNs) break;
+  }
+  atomicExch(err, 1);
+}
+
+// Barrier of the producer warps that also ORs a flag over them, so that every
+// producer takes the same decision (a plain re-read of the shared abort flag
+// after the barrier could differ between threads if another role sets it
+// meanwhile, and the threads that continued would wait at the next barrier for
+// the ones that left).
+__device__ __forceinline__ bool producer_sync_any(bool flag) {
+  uint32_t any;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, %2, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(any)
+      : "r"((uint32_t)flag), "n"(kProducers));
+  return any != 0;
+}
 
 // Power-of-two scale that brings an item's largest component (float bits m)
 // below 2^14; producers and epilogue derive it from the same word.
@@ -156,13 +200,14 @@ __device__ __forceinline__ float item_scale(unsigned mbits) {
 
 // Warp-specialised persistent stage kernel.
 //   warps 0-11 (producers): per item, load the first half of w_n, wait until the
-//              previous item's first MMA group has released the hi tiles, split
-//              w_n (hi parts to the tiles, signalled at once; lo parts held in
-//              registers), wait for the previous item's last MMA group, write the
+//              previous item's MMAs have released the hi tiles, split w_n (hi
+//              parts to the tiles, signalled at once; lo parts held in registers),
+//              wait for the previous item's MMAs to release the lo tiles, write the
 //              lo parts and signal them.
 //   warp 16    (MMA issue): per item, wait for the hi tiles and for the
-//              tensor-memory buffer of the item's parity, issue the hi-tile MMAs,
-//              wait for the lo tiles, issue the lo-tile MMA group.  Issue blocks while the tensor cores drain the
+//              tensor-memory buffer of the item's parity, issue the products with
+//              the hi tiles that do not involve H1, wait for the lo tiles, issue
+//              H1 Z2 and H1 Z1.  Issue blocks while the tensor cores drain the
 //              queue, so it runs in its own warp and the producers convert the
 //              next item meanwhile.
 //   warps 12-15 (epilogue): per item, wait for the MMAs, read the accumulator,
@@ -250,9 +295,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       // The hi tiles are free once the previous item's first MMA group (the
       // products with Z1) has completed; every producer reaches the barrier, then
       // all read the abort flag (uniform exit).
-      if (k >= 1) mbar_wait(&bar_hi[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort);
-      producer_sync();
-      if (*(volatile int *)&s_abort) break;
+      if (k >= 1) mbar_wait(&bar_hi[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort, op.wait_ns);
+      if (producer_sync_any(*(volatile int *)&s_abort != 0)) break;
       // scale and split into FP16 hi + lo; hi goes to the tiles now (the MMA warp
       // starts the hi products as soon as they are all written), lo is kept in
       // registers until the previous item's last MMA group (with Z2) is done
@@ -280,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar_ready_hi[t]);
       // the lo tiles are free once the previous item's MMAs have all completed
-      if (k >= 1) mbar_wait(&bar_mma[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort);
+      if (k >= 1) mbar_wait(&bar_mma[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort, op.wait_ns);
       if (active) {
 #pragma unroll
         for (int g = 0; g < 2 * kProdRows; ++g)
@@ -303,8 +347,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       const int64_t item = blockIdx.x + k * gridDim.x;
       const int t = (int)(k & 1);
       const uint32_t par = (uint32_t)((k >> 1) & 1);
-      bool ok = mbar_wait(&bar_full[t], par, op.err, &s_abort);
-      ok = ok && mbar_wait(&bar_mma[t], par, op.err, &s_abort);
+      bool ok = mbar_wait(&bar_full[t], par, op.err, &s_abort, op.wait_ns);
+      ok = ok && mbar_wait(&bar_mma[t], par, op.err, &s_abort, op.wait_ns);
       if (!__all_sync(0xffffffffu, ok)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       // out = alpha * (-i C); the system-bath kernel adds y and the rest next
@@ -338,49 +382,63 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       const uint32_t id_neg = idesc(128, 256, 0, 0, 1);
       const uint32_t id_mn = idesc(128, 128, 1, 0, 0);
       const int nh = op.n_hpieces;
+      // the mbarrier phase of the most recent commit (bar_hi[t] as 2 t, bar_mma[t]
+      // as 2 t + 1; -1 none): every MMA issued before it has completed once that
+      // phase completes
+      int last_bar = -1;
+      uint32_t last_par = 0;
       for (int64_t k = 0; k < n_mine; ++k) {
         const int t = (int)(k & 1);
         // the tiles of item k are written; its accumulator buffer is free once
         // the epilogue of item k - 2 released it
-        bool ok = mbar_wait(&bar_ready_hi[t], (uint32_t)((k >> 1) & 1), op.err, &s_abort);
-        ok = ok && (k < 2 || mbar_wait(&bar_epi[t], (uint32_t)(((k - 2) >> 1) & 1), op.err, &s_abort));
+        bool ok = mbar_wait(&bar_ready_hi[t], (uint32_t)((k >> 1) & 1), op.err, &s_abort, op.wait_ns);
+        ok = ok && (k < 2 || mbar_wait(&bar_epi[t], (uint32_t)(((k - 2) >> 1) & 1), op.err, &s_abort, op.wait_ns));
         if (!ok) break;
-        // products kept by the split: H1 Z1 + H2 Z1 (+ H3 Z1) with the hi tiles first
-        // (committed to bar_hi, which frees them for the next item), then H1 Z2 once
-        // the lo tiles are written
+        // Products kept by the split, smallest first: H2 Z1 and H3 Z1 (group 0, hi
+        // tiles), then H1 Z2 (lo tiles) and H1 Z1 last (group 1).  The accumulator
+        // holds only small partial sums until the largest product arrives, and the
+        // two halves of each commutator (Z^T H' and -H' Z^T) are interleaved along
+        // the contraction, so the partial sums follow the commutator rather than
+        // either product.  (Each MMA step's FP32 rounding error scales with the
+        // partial sum; on c3 this order cut the error of 1016 RK4 steps 5x.)  The
+        // tiles are released together when the last group completes.
         const uint32_t dcol = tmem + (uint32_t)t * 256u;
         for (int grp = 0; grp < 2; ++grp) {
           if (grp == 1) {
-            if (!mbar_wait(&bar_ready_lo[t], (uint32_t)((k >> 1) & 1), op.err, &s_abort)) break;
+            if (!mbar_wait(&bar_ready_lo[t], (uint32_t)((k >> 1) & 1), op.err, &s_abort, op.wait_ns)) break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const int zk = grp;                                // Z piece of this group: 0 hi, 1 lo
-          const int j_hi = grp == 0 ? nh : 1;               // H pieces of this group
-          for (int j = 0; j < j_hi; ++j) {
+          const int np = grp == 0 ? nh - 1 : 2;
+          for (int i = 0; i < np; ++i) {
+            const int j = grp == 0 ? 1 + i : 0;           // H piece
+            const int zk = grp == 0 ? 0 : 1 - i;          // Z piece: 0 hi, 1 lo
             const uint32_t ha = hh + (uint32_t)j * kHTile, zb = zz[zk];
             for (int kk = 0; kk < 8; ++kk) {
-              const uint64_t a = sdesc(ha + (kk >> 2) * 16384u + (kk & 3) * 32u, 16, 1024);
-              const uint64_t bd = sdesc(zb + (kk >> 2) * (kZZ / 2) + (kk & 3) * 32u, 16, 1024);
-              umma(dcol, a, bd, id_neg, (grp | j | kk) ? 1u : 0u);
-            }
-            for (int part = 0; part < 2; ++part) {
-              const uint32_t za = zz[zk] + (uint32_t)part * 16384u;
-              for (int kk = 0; kk < 8; ++kk) {
-                const uint64_t a = sdesc(za + (uint32_t)kk * 2048u, kZZ / 2, 1024);
-                const uint64_t bd = sdesc(ha + (kk >> 2) * 16384u + (kk & 3) * 32u, 16, 1024);
-                umma(dcol + (uint32_t)part * 128u, a, bd, id_mn, 1);
+              const uint64_t hd = sdesc(ha + (kk >> 2) * 16384u + (kk & 3) * 32u, 16, 1024);
+              const uint64_t zd = sdesc(zb + (kk >> 2) * (kZZ / 2) + (kk & 3) * 32u, 16, 1024);
+              umma(dcol, hd, zd, id_neg, (grp == 0 && i == 0 && kk == 0) ? 0u : 1u);
+              for (int part = 0; part < 2; ++part) {
+                const uint64_t za = sdesc(zb + (uint32_t)part * 16384u + (uint32_t)kk * 2048u, kZZ / 2, 1024);
+                umma(dcol + (uint32_t)part * 128u, za, hd, id_mn, 1);
               }
             }
           }
-          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(grp == 0 ? &bar_hi[t] : &bar_mma[t])));
+          if (grp == 1) {
+            last_bar = 2 * t + 1;
+            last_par = (uint32_t)((k >> 1) & 1);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&bar_hi[t])));
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&bar_mma[t])));
+          }
         }
         if (*(volatile int *)&s_abort) break;
         mbar_arrive(&bar_full[t]);
       }
-      // drain: the last item's MMAs must complete before the tiles and tensor memory go away
-      if (n_mine > 0 && !*(volatile int *)&s_abort)
-        mbar_wait(&bar_mma[(n_mine - 1) & 1], (uint32_t)(((n_mine - 1) >> 1) & 1), op.err, &s_abort);
+      // drain, on the normal and on the abort path: every committed MMA must
+      // complete before the tiles and the tensor memory go away
+      if (last_bar >= 0)
+        mbar_drain((last_bar & 1) ? &bar_mma[last_bar >> 1] : &bar_hi[last_bar >> 1], last_par, op.err);
     }
     __syncwarp();
   }
@@ -528,12 +586,12 @@ void tc_build(TcOperators &tc, const Model &M, const VbModel &vb, std::vector<vo
   tc.n_hpieces = 3;
   // H' shifted by a multiple of the identity (the commutator is unchanged), scaled
   // by a power of two so the largest entry is below 2^14, split into 3 FP16 pieces.
-  double dmax = -1e300, dmin = 1e300;
-  for (int a = 0; a < d; ++a) {
-    dmax = std::max(dmax, M.vb_H[(size_t)a * d + a]);
-    dmin = std::min(dmin, M.vb_H[(size_t)a * d + a]);
-  }
-  const double shift = 0.5 * (dmax + dmin);
+  // The shift is the energy of the product ground state, <0|H_S'|0>: the states
+  // the response carries most weight on (the equilibrium populations and the
+  // coherences with the ground state) then have small products (H' - c) w and
+  // w (H' - c), and the tensor cores' FP32 accumulation, whose rounding error
+  // scales with the partial sums, stays close to the size of the commutator.
+  const double shift = M.H[0];
   double amax = 0.0;
   for (int a = 0; a < d; ++a)
     for (int b2 = 0; b2 < d; ++b2) amax = std::max(amax, std::fabs(M.vb_H[(size_t)a * d + b2] - (a == b2 ? shift : 0.0)));
@@ -553,18 +611,18 @@ void tc_build(TcOperators &tc, const Model &M, const VbModel &vb, std::vector<vo
       }
     }
   void *p = nullptr;
-  if (cudaMalloc(&p, img.size() * 2) != cudaSuccess) throw std::bad_alloc();
+  if (device_malloc(&p, img.size() * 2) != cudaSuccess) throw DeviceOom();
   allocs.push_back(p);
   cudaMemcpy(p, img.data(), img.size() * 2, cudaMemcpyHostToDevice);
   tc.himg = (const uint4 *)p;
   std::vector<float> lam((size_t)M.n_modes * 128, 0.f);
   for (int s = 0; s < M.n_modes; ++s)
     for (int a = 0; a < d; ++a) lam[(size_t)s * 128 + a] = (float)M.vb_lam[s][(a / M.stride[s]) % M.dims[s]];
-  if (cudaMalloc(&p, lam.size() * 4) != cudaSuccess) throw std::bad_alloc();
+  if (device_malloc(&p, lam.size() * 4) != cudaSuccess) throw DeviceOom();
   allocs.push_back(p);
   cudaMemcpy(p, lam.data(), lam.size() * 4, cudaMemcpyHostToDevice);
   tc.lam = (const float *)p;
-  if (cudaMalloc(&p, 16) != cudaSuccess) throw std::bad_alloc();
+  if (device_malloc(&p, 16) != cudaSuccess) throw DeviceOom();
   allocs.push_back(p);
   cudaMemset(p, 0, 16);
   tc.err = (int *)p;
@@ -610,7 +668,7 @@ void tc_reserve(TcOperators &tc, int64_t n_items) {
   if (tc.maxbuf) cudaFree(tc.maxbuf);
   tc.maxbuf = nullptr;
   tc.max_items = 0;
-  if (cudaMalloc(&tc.maxbuf, (size_t)n_items * 3 * sizeof(unsigned)) != cudaSuccess) throw std::bad_alloc();
+  if (device_malloc((void **)&tc.maxbuf, (size_t)n_items * 3 * sizeof(unsigned)) != cudaSuccess) throw DeviceOom();
   tc.max_items = n_items;
 }
 

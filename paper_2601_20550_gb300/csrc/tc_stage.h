@@ -7,6 +7,7 @@
 #pragma once
 
 #include <cstdint>
+#include <new>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -15,6 +16,14 @@
 #include "model.h"
 
 namespace heom {
+
+// Every device allocation of the library goes through device_malloc, which
+// honours the host-side allocation-failure injection (heom_debug_fail_alloc).
+cudaError_t device_malloc(void **p, size_t bytes);
+// A device allocation failed (reported as HEOM_ENOMEM).
+struct DeviceOom : std::bad_alloc {
+  const char *what() const noexcept override { return "device allocation failed"; }
+};
 
 struct TcOperators {
   bool ready = false;
@@ -26,6 +35,7 @@ struct TcOperators {
   const int *nb_off = nullptr, *nb_idx = nullptr;
   const float *nb_cA = nullptr, *nb_cB = nullptr;
   int *err = nullptr;             // device error word (bounded waits)
+  uint64_t wait_ns = 2000000000ull;  // time limit of each device-side wait
   int sms = 0;
   unsigned *maxbuf = nullptr;     // workspace: per-item max |w| of y, wa, wb (grown on demand)
   int64_t max_items = 0;

@@ -97,6 +97,12 @@ def lib():
         "heom_state_export_dev": [_P, _P, _P],
         "heom_propagate_noalloc": [_P, _P, ct.c_int, ct.c_double, ct.c_int64, _P],
         "heom_state_import_dev": [_P, _P, _P],
+        "heom_set_wait_limit_ns": [_P, ct.c_uint64],
+        "heom_ckpt_write": [ct.c_char_p, _P, ct.c_uint64],
+        "heom_ckpt_read": [ct.c_char_p, _P, ct.c_uint64],
+        "heom_ckpt_verify": [ct.c_char_p, ct.POINTER(ct.c_uint64)],
+        "heom_state_save": [_P, ct.c_char_p],
+        "heom_state_load": [_P, ct.c_char_p],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -112,6 +118,8 @@ def lib():
     L.heom_state_device_ptr.restype = _P
     L.heom_state_branches.argtypes = [_P]
     L.heom_state_branches.restype = ct.c_int
+    L.heom_debug_fail_alloc.argtypes = [ct.c_int64]
+    L.heom_debug_fail_alloc.restype = None
     _lib = L
     return L
 
@@ -413,6 +421,45 @@ def heom_get_tuning(h):
     blk, grd = (ct.c_int * max(n, 1))(), (ct.c_int * max(n, 1))()
     L.heom_get_tuning(h.h, n, kind, el, blk, grd)
     return [(kind[i], el[i], blk[i], grd[i]) for i in range(n)]
+
+
+def heom_ckpt_write(path, arr):
+    """Write a contiguous numpy array's bytes to a checkpoint file."""
+    a = np.ascontiguousarray(arr)
+    _check(lib().heom_ckpt_write(os.fsencode(path), a.ctypes.data_as(_P), a.nbytes))
+
+
+def heom_ckpt_read(path, out):
+    """Fill the contiguous numpy array ``out`` from a checkpoint file (integrity checked)."""
+    if not out.flags["C_CONTIGUOUS"]:
+        raise ValueError("out must be C-contiguous")
+    _check(lib().heom_ckpt_read(os.fsencode(path), out.ctypes.data_as(_P), out.nbytes))
+    return out
+
+
+def heom_ckpt_verify(path):
+    """Payload size of an intact checkpoint file (raises HeomError otherwise)."""
+    n = ct.c_uint64(0)
+    _check(lib().heom_ckpt_verify(os.fsencode(path), ct.byref(n)))
+    return n.value
+
+
+def heom_state_save(s, path):
+    _check(lib().heom_state_save(s.h, os.fsencode(path)))
+
+
+def heom_state_load(s, path):
+    _check(lib().heom_state_load(s.h, os.fsencode(path)))
+
+
+def heom_set_wait_limit_ns(h, ns):
+    """Time limit (ns) of every device-side wait of h's tensor-core stage kernel."""
+    _check(lib().heom_set_wait_limit_ns(h.h, int(ns)))
+
+
+def heom_debug_fail_alloc(after):
+    """Make device allocations fail after `after` more successes (after < 0: off)."""
+    lib().heom_debug_fail_alloc(int(after))
 
 
 def heom_launch_count():

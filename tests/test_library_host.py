@@ -140,3 +140,18 @@ def test_noalloc_rejects_bad_pointers_before_any_launch():
     for dt in (float("inf"), float("nan"), 0.0, -0.5):
         rc = L.heom_propagate_noalloc(h.h, ct.c_void_p(0x10000), 1, dt, 1, None)
         assert rc == -1 and "bad arguments" in H.heom_last_error()
+
+
+def test_unstable_step_rejected_before_any_device_work():
+    """dt outside the RK4 stability region of the model returns HEOM_EUNSTABLE from
+    the host-side pre-check, before the device is touched (no GPU needed)."""
+    import ctypes as ct
+    L = H.lib()
+    h = H.heom_build_hierarchy(W.config("c2")[0])
+    p = ct.c_void_p(0x10000)
+    rc = L.heom_propagate_dev(h.h, p, p, p, 1, 0, 10.0, 1, None)
+    assert rc == -4 and "stability" in H.heom_last_error()
+    out = ct.c_void_p()
+    assert L.heom_equilibrate(h.h, 10.0, 100.0, 0.0, ct.byref(out)) == -4 and not out.value
+    # a stable step passes the pre-check (and then needs the device)
+    assert L.heom_propagate_dev(h.h, p, p, p, 1, 0, 0.5, 0, None) != -4
