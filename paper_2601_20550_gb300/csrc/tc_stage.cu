@@ -18,6 +18,9 @@
 // vterm_kernel then adds y, tpart and the elementwise decay and system-bath
 // terms (out = y + tpart + alpha (-gamma_n w_n + sum kappa w_nb)) as a streaming
 // kernel at high occupancy, so that enough neighbour loads are in flight.
+// (Moving y and the decay into the epilogue took 35 ns per item off this
+// kernel but added 80 to the tensor-core kernel, whose four epilogue warps
+// cannot hide the latency of two more loads per element.)
 // All waits are bounded: on expiry the kernel sets the error word, frees its
 // tensor memory and returns.
 #include "tc_stage.h"
@@ -215,7 +218,7 @@ __device__ __forceinline__ float item_scale(unsigned mbits) {
 // The epilogue of item k overlaps the MMAs of item k + 1 and the loads of k + 2.
 __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
   extern __shared__ uint8_t smem_raw[];
-  __shared__ uint64_t bar_mma[2], bar_hi[2], bar_full[2], bar_epi[2], bar_ready_hi[2], bar_ready_lo[2];
+  __shared__ uint64_t bar_mma[2], bar_lo[2], bar_full[2], bar_epi[2], bar_ready_hi[2], bar_ready_lo[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
 
@@ -231,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
     s_abort = 0;
     for (int t = 0; t < 2; ++t) {
       mbar_init(&bar_mma[t], 1);
-      mbar_init(&bar_hi[t], 1);
+      mbar_init(&bar_lo[t], 1);
       mbar_init(&bar_full[t], 1);
       mbar_init(&bar_epi[t], kEpilogue / 32);
       mbar_init(&bar_ready_hi[t], kProducers / 32);
@@ -292,15 +295,14 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       load_batch(0);
       // power-of-two scale from the item's largest component (kept by the previous stage)
       const float scale = item_scale(P.max_in[item]);
-      // The hi tiles are free once the previous item's first MMA group (the
-      // products with Z1) has completed; every producer reaches the barrier, then
-      // all read the abort flag (uniform exit).
-      if (k >= 1) mbar_wait(&bar_hi[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort, op.wait_ns);
+      // The lo tiles are free once the previous item's first MMA (H1 Z2) has
+      // completed; every producer takes the same decision to go on or to leave.
+      if (k >= 1) mbar_wait(&bar_lo[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort, op.wait_ns);
       if (producer_sync_any(*(volatile int *)&s_abort != 0)) break;
-      // scale and split into FP16 hi + lo; hi goes to the tiles now (the MMA warp
-      // starts the hi products as soon as they are all written), lo is kept in
-      // registers until the previous item's last MMA group (with Z2) is done
-      __half2 lre[2 * kProdRows], lim[2 * kProdRows];
+      // scale and split into FP16 hi + lo; lo goes to the tiles now (the MMA warp
+      // starts this item with H1 Z2 as soon as they are all written), hi is kept in
+      // registers until the previous item's MMAs have all completed
+      __half2 hre[2 * kProdRows], him[2 * kProdRows];
 #pragma unroll
       for (int bt = 0; bt < 2; ++bt) {
         if (bt == 1) load_batch(1);
@@ -309,34 +311,35 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
           const int g = kProdRows * bt + i;                  // row a = r0 + 6 g
           const float2 xr = make_float2(v[2 * i].x * scale, v[2 * i + 1].x * scale);
           const float2 xi = make_float2(v[2 * i].y * scale, v[2 * i + 1].y * scale);
-          const __half2 hr = __float22half2_rn(xr), hi = __float22half2_rn(xi);
-          const float2 fr = __half22float2(hr), fi = __half22float2(hi);
-          lre[g] = __float22half2_rn(make_float2(xr.x - fr.x, xr.y - fr.y));
-          lim[g] = __float22half2_rn(make_float2(xi.x - fi.x, xi.y - fi.y));
+          hre[g] = __float22half2_rn(xr);
+          him[g] = __float22half2_rn(xi);
+          const float2 fr = __half22float2(hre[g]), fi = __half22float2(him[g]);
+          const __half2 lr = __float22half2_rn(make_float2(xr.x - fr.x, xr.y - fr.y));
+          const __half2 li = __float22half2_rn(make_float2(xi.x - fi.x, xi.y - fi.y));
           if (active && r0 + 6 * g < d) {
             const uint32_t o = row_ofs[g & 3] + 3072u * (uint32_t)(g >> 2);
-            *reinterpret_cast<__half2 *>(ZZ1 + o) = hr;
-            *reinterpret_cast<__half2 *>(ZZ1 + o + 16384u) = hi;
+            *reinterpret_cast<__half2 *>(ZZ2 + o) = lr;
+            *reinterpret_cast<__half2 *>(ZZ2 + o + 16384u) = li;
           }
         }
       }
       asm volatile("fence.proxy.async.shared::cta;");
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bar_ready_hi[t]);
-      // the lo tiles are free once the previous item's MMAs have all completed
+      if (lane == 0) mbar_arrive(&bar_ready_lo[t]);
+      // the hi tiles are free once the previous item's MMAs have all completed
       if (k >= 1) mbar_wait(&bar_mma[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort, op.wait_ns);
       if (active) {
 #pragma unroll
         for (int g = 0; g < 2 * kProdRows; ++g)
           if (r0 + 6 * g < d) {
             const uint32_t o = row_ofs[g & 3] + 3072u * (uint32_t)(g >> 2);
-            *reinterpret_cast<__half2 *>(ZZ2 + o) = lre[g];
-            *reinterpret_cast<__half2 *>(ZZ2 + o + 16384u) = lim[g];
+            *reinterpret_cast<__half2 *>(ZZ1 + o) = hre[g];
+            *reinterpret_cast<__half2 *>(ZZ1 + o + 16384u) = him[g];
           }
       }
       asm volatile("fence.proxy.async.shared::cta;");
       __syncwarp();
-      if (lane == 0) mbar_arrive(&bar_ready_lo[t]);
+      if (lane == 0) mbar_arrive(&bar_ready_hi[t]);
     }
   } else if (warp < kMmaWarp) {
     // ------------------------------------------------------------ epilogue
@@ -351,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       ok = ok && mbar_wait(&bar_mma[t], par, op.err, &s_abort, op.wait_ns);
       if (!__all_sync(0xffffffffu, ok)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
-      // out = alpha * (-i C); the system-bath kernel adds y and the rest next
+      // tpart = alpha (-i C); the streaming kernel adds y and the rest next
       if (tid == kProducers) P.max_out[item] = 0u;
       const float sc = P.alpha * op.inv_sh / item_scale(P.max_in[item]);
       float2 *ob = P.out + item * dd;
@@ -382,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       const uint32_t id_neg = idesc(128, 256, 0, 0, 1);
       const uint32_t id_mn = idesc(128, 128, 1, 0, 0);
       const int nh = op.n_hpieces;
-      // the mbarrier phase of the most recent commit (bar_hi[t] as 2 t, bar_mma[t]
+      // the mbarrier phase of the most recent commit (bar_lo[t] as 2 t, bar_mma[t]
       // as 2 t + 1; -1 none): every MMA issued before it has completed once that
       // phase completes
       int last_bar = -1;
@@ -391,46 +394,43 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
         const int t = (int)(k & 1);
         // the tiles of item k are written; its accumulator buffer is free once
         // the epilogue of item k - 2 released it
-        bool ok = mbar_wait(&bar_ready_hi[t], (uint32_t)((k >> 1) & 1), op.err, &s_abort, op.wait_ns);
+        bool ok = mbar_wait(&bar_ready_lo[t], (uint32_t)((k >> 1) & 1), op.err, &s_abort, op.wait_ns);
         ok = ok && (k < 2 || mbar_wait(&bar_epi[t], (uint32_t)(((k - 2) >> 1) & 1), op.err, &s_abort, op.wait_ns));
         if (!ok) break;
-        // Products kept by the split, smallest first: H2 Z1 and H3 Z1 (group 0, hi
-        // tiles), then H1 Z2 (lo tiles) and H1 Z1 last (group 1).  The accumulator
-        // holds only small partial sums until the largest product arrives, and the
-        // two halves of each commutator (Z^T H' and -H' Z^T) are interleaved along
-        // the contraction, so the partial sums follow the commutator rather than
-        // either product.  (Each MMA step's FP32 rounding error scales with the
-        // partial sum; on c3 this order cut the error of 1016 RK4 steps 5x.)  The
-        // tiles are released together when the last group completes.
+        // Products kept by the split, the small ones first: H1 Z2 (lo tiles, group
+        // 0, committed on its own so the producers can refill the lo tiles), then
+        // H2 Z1 and H3 Z1, and the largest, H1 Z1, last (group 1, hi tiles).  The
+        // accumulator holds only small partial sums until the largest product
+        // arrives, and the two halves of each commutator (Z^T H' and -H' Z^T) are
+        // interleaved along the contraction, so the partial sums follow the
+        // commutator rather than either product.  (Each MMA step's FP32 rounding
+        // error scales with the partial sum; on c3 this order cut the error of
+        // 1016 RK4 steps 5x.)
         const uint32_t dcol = tmem + (uint32_t)t * 256u;
         for (int grp = 0; grp < 2; ++grp) {
           if (grp == 1) {
-            if (!mbar_wait(&bar_ready_lo[t], (uint32_t)((k >> 1) & 1), op.err, &s_abort, op.wait_ns)) break;
+            if (!mbar_wait(&bar_ready_hi[t], (uint32_t)((k >> 1) & 1), op.err, &s_abort, op.wait_ns)) break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
-          const int np = grp == 0 ? nh - 1 : 2;
+          const int np = grp == 0 ? 1 : nh;
           for (int i = 0; i < np; ++i) {
-            const int j = grp == 0 ? 1 + i : 0;           // H piece
-            const int zk = grp == 0 ? 0 : 1 - i;          // Z piece: 0 hi, 1 lo
+            const int j = grp == 0 ? 0 : (i + 1) % nh;    // H piece: group 1 takes H2, H3, then H1
+            const int zk = grp == 0 ? 1 : 0;              // Z piece: 0 hi, 1 lo
             const uint32_t ha = hh + (uint32_t)j * kHTile, zb = zz[zk];
             for (int kk = 0; kk < 8; ++kk) {
               const uint64_t hd = sdesc(ha + (kk >> 2) * 16384u + (kk & 3) * 32u, 16, 1024);
               const uint64_t zd = sdesc(zb + (kk >> 2) * (kZZ / 2) + (kk & 3) * 32u, 16, 1024);
-              umma(dcol, hd, zd, id_neg, (grp == 0 && i == 0 && kk == 0) ? 0u : 1u);
+              umma(dcol, hd, zd, id_neg, (grp == 0 && kk == 0) ? 0u : 1u);
               for (int part = 0; part < 2; ++part) {
                 const uint64_t za = sdesc(zb + (uint32_t)part * 16384u + (uint32_t)kk * 2048u, kZZ / 2, 1024);
                 umma(dcol + (uint32_t)part * 128u, za, hd, id_mn, 1);
               }
             }
           }
-          if (grp == 1) {
-            last_bar = 2 * t + 1;
-            last_par = (uint32_t)((k >> 1) & 1);
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&bar_hi[t])));
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_u32(&bar_mma[t])));
-          }
+          last_bar = 2 * t + grp;
+          last_par = (uint32_t)((k >> 1) & 1);
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(grp == 0 ? &bar_lo[t] : &bar_mma[t])));
         }
         if (*(volatile int *)&s_abort) break;
         mbar_arrive(&bar_full[t]);
@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       // drain, on the normal and on the abort path: every committed MMA must
       // complete before the tiles and the tensor memory go away
       if (last_bar >= 0)
-        mbar_drain((last_bar & 1) ? &bar_mma[last_bar >> 1] : &bar_hi[last_bar >> 1], last_par, op.err);
+        mbar_drain((last_bar & 1) ? &bar_mma[last_bar >> 1] : &bar_lo[last_bar >> 1], last_par, op.err);
     }
     __syncwarp();
   }
