@@ -250,7 +250,8 @@ void check_tc_error(heom_hier *h) {
   int e = 0;
   CUDA_TRY(cudaMemcpy(&e, h->tc.err, sizeof(int), cudaMemcpyDeviceToHost));
   if (e) {
-    CUDA_TRY(cudaMemset(h->tc.err, 0, sizeof(int)));
+    CUDA_TRY(cudaMemsetAsync(h->tc.err, 0, sizeof(int), h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
     throw Fail{HEOM_ETIMEOUT, "a tensor-core stage wait ran out"};
   }
 }
@@ -353,7 +354,9 @@ void ensure_device(heom_hier *h) {
   Model &M = h->M;
   // (a set-up that failed part-way is redone from the start by the next call;
   // what it allocated stays owned by the handle)
-  if (!h->stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  // a blocking stream: ordered with work on the legacy default stream, so a state
+  // zeroed or filled there before a call is seen by the call's kernels
+  if (!h->stream) CUDA_TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamDefault));
   std::vector<double> vl;
   DevModel<double> d64{};
   d64.d = M.d;
@@ -424,6 +427,8 @@ void ensure_device(heom_hier *h) {
   vb.nb_cB = d32.nb_cB;
   h->vb = vb;
   if (M.precision == HEOM_TC) tc_build(h->tc, M, h->vb, h->allocs);
+  // the table uploads above are complete before any launch on any stream
+  CUDA_TRY(cudaDeviceSynchronize());
   h->on_device = true;
 }
 
@@ -515,7 +520,10 @@ heom_status heom_state_create(const heom_hier *h, int branches, int precision, h
     s->hier = const_cast<heom_hier *>(h);
     try {
       s->buf.alloc(s->elems() * s->elem_bytes());
-      CUDA_TRY(cudaMemset(s->buf.p, 0, s->buf.bytes));
+      // zeroed on the hierarchy's stream and complete before the call returns, so
+      // that work the caller issues next, on any stream, sees the zeros
+      CUDA_TRY(cudaMemsetAsync(s->buf.p, 0, s->buf.bytes, h->stream));
+      CUDA_TRY(cudaStreamSynchronize(h->stream));
     } catch (...) {
       delete s;
       throw;
@@ -531,12 +539,14 @@ heom_status heom_state_upload(heom_state *s, const double *host) {
   if (!s || !host) return fail(HEOM_EINVAL, "null argument");
   return guarded([&]() -> heom_status {
     const int64_t n = s->elems();
+    cudaStream_t st = s->hier->stream;
     if (s->precision == HEOM_FP64) {
-      CUDA_TRY(cudaMemcpy(s->buf.p, host, n * 16, cudaMemcpyHostToDevice));
+      CUDA_TRY(cudaMemcpyAsync(s->buf.p, host, n * 16, cudaMemcpyHostToDevice, st));
+      CUDA_TRY(cudaStreamSynchronize(st));
     } else {
       DeviceBuffer tmp(n * 16);
-      CUDA_TRY(cudaMemcpy(tmp.p, host, n * 16, cudaMemcpyHostToDevice));
-      to_coupling_basis(s->hier, (const double2 *)tmp.p, (float2 *)s->buf.p, n, s->hier->stream);
+      CUDA_TRY(cudaMemcpyAsync(tmp.p, host, n * 16, cudaMemcpyHostToDevice, st));
+      to_coupling_basis(s->hier, (const double2 *)tmp.p, (float2 *)s->buf.p, n, st);
     }
     return HEOM_OK;
   });
@@ -643,7 +653,7 @@ heom_status heom_equilibrate(heom_hier *h, double dt_fs, double t_max_fs, double
     const Model &M = h->M;
     const int64_t per = (int64_t)M.n_ado * M.d * M.d;
     double one[2] = {1.0, 0.0};
-    CUDA_TRY(cudaMemcpy(s->buf.p, one, 16, cudaMemcpyHostToDevice));   // rho_0 = |0><0|
+    CUDA_TRY(cudaMemcpyAsync(s->buf.p, one, 16, cudaMemcpyHostToDevice, h->stream));   // rho_0 = |0><0|
     DeviceBuffer a(per * 16), b(per * 16);
     const int64_t nmax = (int64_t)std::llround(t_max_fs / dt_fs);
     s->eq_dt = dt_fs;
@@ -654,7 +664,7 @@ heom_status heom_equilibrate(heom_hier *h, double dt_fs, double t_max_fs, double
       return HEOM_OK;
     }
     DeviceBuffer norms((size_t)M.n_ado * 8), zero(per * 16);
-    CUDA_TRY(cudaMemset(zero.p, 0, per * 16));
+    CUDA_TRY(cudaMemsetAsync(zero.p, 0, per * 16, h->stream));
     std::vector<double> hn(M.n_ado);
     int64_t done = 0;
     while (done < nmax) {

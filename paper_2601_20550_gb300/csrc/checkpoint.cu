@@ -159,6 +159,7 @@ heom_status heom_state_save(const heom_state *s, const char *path) {
   return guarded([&]() -> heom_status {
     const uint64_t bytes = (uint64_t)s->elems() * s->elem_bytes();
     std::vector<unsigned char> host(bytes);
+    CUDA_TRY(cudaDeviceSynchronize());   // work on any stream that writes the state is done
     CUDA_TRY(cudaMemcpy(host.data(), s->buf.p, bytes, cudaMemcpyDeviceToHost));
     unsigned char tag[kTagBytes] = {0};
     StateTag t{s->branches, s->precision, s->d, s->n_ado, s->eq_steps, s->eq_dt};
@@ -181,6 +182,7 @@ heom_status heom_state_load(heom_state *s, const char *path) {
     });
     // the device state changes only once the whole file has passed its check
     CUDA_TRY(cudaMemcpy(s->buf.p, host.data(), bytes, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaDeviceSynchronize());   // complete before work on any stream reads it
     s->eq_steps = t.eq_steps;
     s->eq_dt = t.eq_dt;
     return HEOM_OK;

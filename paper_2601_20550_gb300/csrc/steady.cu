@@ -82,7 +82,7 @@ extern "C" heom_status heom_steady_state(heom_hier *h, double tol, int restart, 
     const int m = restart;
     double2 *x = (double2 *)s->buf.p;
     const double one[2] = {1.0, 0.0};
-    CUDA_TRY(cudaMemcpy(x, one, 16, cudaMemcpyHostToDevice));   // x = |0><0|, tr x_0 = 1
+    CUDA_TRY(cudaMemcpyAsync(x, one, 16, cudaMemcpyHostToDevice, st));   // x = |0><0|, tr x_0 = 1
     DeviceBuffer V((size_t)(m + 1) * n * 16), w((size_t)n * 16), partial((size_t)kKrylovBlocks * (m + 1) * 16),
         coef((size_t)(m + 1) * 16);
     double2 *Vp = (double2 *)V.p, *wp = (double2 *)w.p;

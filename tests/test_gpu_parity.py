@@ -435,3 +435,28 @@ def test_c5_full_size_step_sampled():
     k4 = OH.rhs_one(prob, getter(u4), n)
     ref = (x + dt / 6.0 * (k1[n] + 2 * k2[n] + 2 * k3[n] + k4))[0]
     assert rel(got, ref) < 1e-11
+
+
+@pytest.mark.gpu
+def test_state_creation_ordered_after_pending_work():
+    """A state created and filled while earlier GPU work is still queued on the
+    caller's (legacy default) stream keeps its contents: the library zeroes new
+    states on its own stream before the call returns, and its stream is ordered
+    with the legacy stream.  (A zeroing memset left on the legacy stream once
+    landed after the broadcast into the new state.)"""
+    torch = pytest.importorskip("torch")
+    model = W.small_three_mode(n=3, depth_L=2)
+    for precision in (0, 2):
+        h = H.heom_build_hierarchy(model, precision)
+        eq = H.heom_equilibrate(h, 0.5, 10.0, 0.0)
+        ref = H.heom_state_download(eq)
+        a = torch.randn(8192, 8192, device="cuda:0")
+        for _ in range(24):          # queued work (hundreds of ms), not synchronised
+            a = a @ a
+            a = a / a.norm()
+        s = H.heom_state_create(h, 2, precision)
+        H.heom_state_broadcast(eq, s)
+        got = H.heom_state_download(s)
+        torch.cuda.synchronize()
+        assert np.abs(got[0] - ref[0]).max() < 1e-6 * np.abs(ref).max()
+        assert np.abs(got[1] - ref[0]).max() < 1e-6 * np.abs(ref).max()
