@@ -79,6 +79,9 @@ def algorithmic_costs(model, d, nado, ado_table, nb_counts, prec):
     flops: 4 stages x ([H, w] with a real H: 8 d^3; per mode s the neighbour sums
     (8 d^2 per coupling entry) and V_s applied to A_s, B_s from both sides
     (16 d^2 n_s); decay and update 8 d^2).
+    The byte count is that of the classic tableau; the nested (Horner) form the
+    library runs needs 11 d^2 b (each stage reads its input and y and writes its
+    output; the last stage reads y once), which the caller reports beside it.
     """
     dims = [md["n_levels"] for md in model["modes"]]
     avg_nb = nb_counts.sum(axis=0) / nado   # per mode
@@ -91,8 +94,9 @@ def algorithmic_costs(model, d, nado, ado_table, nb_counts, prec):
 
 
 # Measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per work item
-# (one ADO of one branch) of one RK4 stage of the tensor-core path, from the ncu
-# capture summarised in profiles/tc_stage_c3.md (4-branch case, scaled per item).
+# (one ADO of one branch) of one RK4 stage of the tensor-core path: one ncu capture
+# of a 4-branch c3 case, scaled per item (the per-branch working set is the same at
+# 256 branches).  None when the stage kernels have changed since that capture.
 TC_STAGE_TRAFFIC_BYTES_PER_ITEM = 753.4e3
 
 
@@ -211,7 +215,7 @@ def run_reference(args, cfg, rank, world):
             "warmup": args.warmup, "ms_per_step": 1000.0 * float(np.mean([v["seconds"] for v in vals])),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded water-like MAB model)",
-            "config": conf,
+            "config": dict(conf, precision="f64"),
             "cpu_baseline": {"value": value, "unit": "ADO-updates/s", "cores": os.cpu_count(),
                              "kind": "oracle", "sample": vals[0]["sample"]},
             "e2e": {"value": value, "unit": "ADO-updates/s", "h2d_bytes_per_step": 0,
@@ -251,6 +255,34 @@ def run_grad(args, local):
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
     launches = H.heom_launch_count() - n_launch0
+    # optional check against Richardson-extrapolated central differences of the
+    # library's own FP64 loss (step 1e-3 |theta_i| and half of it: O(step^4))
+    fd_check = None
+    if args.grad_fd > 0:
+        def lib_loss(t):
+            hh = H.heom_build_hierarchy(H.with_theta(model, t), 0)
+            e = H.heom_equilibrate(hh, grid["dt_fs"], grid["t_eq_fs"], 0.0)
+            return float(np.sum((H.heom_response_2d(hh, e, grid)[2] - S_ref) ** 2))
+
+        w = np.maximum(np.abs(th), 1.0)
+
+        def central(i, step):
+            tp, tm = th.copy(), th.copy()
+            tp[i] += step
+            tm[i] -= step
+            return (lib_loss(tp) - lib_loss(tm)) / (2 * step)
+
+        scale = float(np.max(np.abs(g * w)))
+        entries = []
+        t_fd = time.perf_counter()
+        for i in (0, 4, 7, 10)[:args.grad_fd]:
+            step = 1e-3 * w[i]
+            fd = (4 * central(i, step / 2) - central(i, step)) / 3
+            entries.append({"theta": i, "adjoint": float(g[i]), "fd": float(fd),
+                            "rel_err": abs(g[i] - fd) / max(abs(fd), 1e-300),
+                            "err_over_max_theta_grad": abs(g[i] - fd) * w[i] / scale})
+        fd_check = {"method": "Richardson central differences of the library's FP64 loss",
+                    "entries": entries, "seconds": time.perf_counter() - t_fd}
     print(json.dumps({
         "metric": "c4 misfit gradient, forward-equivalent HEOM ADO-updates/s", "value": fwd / el,
         "unit": "ADO-updates/s", "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": True,
@@ -258,7 +290,7 @@ def run_grad(args, local):
         "config": {"workload": "c4: 3-mode MAB, d=%d, %d ADOs (L=4), %dx%d t1xt3, t2=0, dt=0.5 fs, m=8, "
                                "12 parameters, checkpoints every 64 steps" % (h.d, nado, n1, n3)},
         "seconds_per_gradient": el, "forward_ado_updates": fwd, "loss": loss,
-        "dtheta": list(map(float, g)), "gpu_launches": int(launches)}))
+        "dtheta": list(map(float, g)), "gpu_launches": int(launches), "fd_check": fd_check}))
 
 
 def run_c5_window(args, local):
@@ -316,6 +348,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--grad-n", type=int, default=16, help="t1 and t3 samples of the c4-grad workload")
+    ap.add_argument("--grad-fd", type=int, default=0,
+                    help="c4-grad: check this many gradient entries (<= 4) against finite differences")
     ap.add_argument("--c5-precision", type=int, default=0, choices=[0, 1], help="c5-window: 0 FP64, 1 FP32")
     ap.add_argument("--branches", type=int, default=0,
                     help="override the batch (profiling runs only; default 2*n1)")
@@ -348,7 +382,13 @@ def main():
     model, grid = W.config(cfg)
     h = H.heom_build_hierarchy(model, prec)
     d, nado = h.d, h.n_ado
+    # the FP64 equilibration of Sec. II.C.1 (timed: its share enters spectra/hour)
+    H.heom_state_create(h, 1, 0)
+    torch.cuda.synchronize()
+    t_eq0 = time.perf_counter()
     eq = H.heom_equilibrate(h, grid["dt_fs"], grid["t_eq_fs"], 0.0)
+    torch.cuda.synchronize()
+    eq_seconds = time.perf_counter() - t_eq0
     m = grid["steps_per_sample"]
     B = args.branches if args.branches > 0 else 2 * grid["n1"]
     cdt = torch.complex128 if prec == 0 else torch.complex64
@@ -443,7 +483,53 @@ def main():
                 "kernel": "RK4 stage (tc_stage_kernel + vterm_kernel)" if prec == 2 else "stage_kernel_vb",
                 "peak_source": "%s hbm_gbs (MEASURED_PEAKS.json)" % peak_kind,
                 "algorithmic_bytes_per_ado_update": bytes_upd,
+                "algorithmic_bytes_basis": "classic RK4 tableau, 20 d^2 b per ADO-update",
+                "frac_nested_form": achieved * (11.0 / 20.0) / peak,
+                "nested_form_bytes_per_ado_update": bytes_upd * 11.0 / 20.0,
                 "flops_TFLOPs": flops_upd * per_launch_units / stage_s / 1e12}
+
+    # ---------------- error against the FP64 path ----------------
+    # (a) the timed traces: every branch of the timed batch started from the same
+    #     kicked state, so one FP64 branch propagated through the same (warm-up +
+    #     timed) sample periods is the reference for all of them;
+    # (b) the full t3 length of the workload (n3 samples of m RK4 steps) on one
+    #     branch in the same precision, against the same FP64 branch continued.
+    # (The FP64 path matches the oracle to 1e-10 on the test models.)
+    error = None
+    if prec != 0 and not args.no_fp64:
+        h64e = H.heom_build_hierarchy(model, 0)
+        s64 = H.heom_state_create(h64e, 1, 0)
+        H.heom_state_broadcast(eq, s64)
+        y1 = torch.empty((1, nado, d, d), dtype=torch.complex128, device=dev)
+        H.heom_kick_dev(h64e, H.heom_state_device_ptr(s64), y1.data_ptr(), 1, 0, 1, sp)
+        a1, b1 = torch.empty_like(y1), torch.empty_like(y1)
+        n3 = grid["n3"]
+        nt = max(n3, args.warmup + args.steps)
+        ref = torch.zeros(nt, dtype=torch.complex128, device=dev)
+        for i in range(nt):
+            H.heom_propagate_dev(h64e, y1.data_ptr(), a1.data_ptr(), b1.data_ptr(), 1, 0,
+                                 grid["dt_fs"], m, sp)
+            H.heom_trace_dev(h64e, y1.data_ptr(), 1, 0, 3, ref[i:i + 1].data_ptr(), sp)
+        # one branch in the benched precision from the same kicked state
+        sM = H.heom_state_create(h, 1, prec)
+        H.heom_state_broadcast(eq, sM)
+        yM = torch.empty((1, nado, d, d), dtype=cdt, device=dev)
+        H.heom_kick_dev(h, H.heom_state_device_ptr(sM), yM.data_ptr(), 1, prec, 1, sp)
+        aM, bM = torch.empty_like(yM), torch.empty_like(yM)
+        trM = torch.zeros(n3, dtype=torch.complex128, device=dev)
+        for i in range(n3):
+            H.heom_propagate_dev(h, yM.data_ptr(), aM.data_ptr(), bM.data_ptr(), 1, prec,
+                                 grid["dt_fs"], m, sp)
+            H.heom_trace_dev(h, yM.data_ptr(), 1, prec, 3, trM[i:i + 1].data_ptr(), sp)
+        torch.cuda.synchronize()
+        nw = args.warmup + args.steps
+        timed = (traces - ref[:nw, None]).abs().max().item() / ref[:nw].abs().max().item()
+        full = (trM - ref[:n3]).abs().max().item() / ref[:n3].abs().max().item()
+        error = {"timed_traces": {"max_abs_over_max_ref": timed, "rk4_steps": nw * m,
+                                  "branches_compared": B},
+                 "full_t3_length": {"max_abs_over_max_ref": full, "rk4_steps": n3 * m, "branches": 1},
+                 "vs": "FP64 GPU path (same kicked initial state, same RK4 steps)"}
+        del y1, a1, b1, s64, h64e, yM, aM, bM, sM
 
     # ---------------- plain FP64 GPU path on the same model (mixed vs FP64) ----------------
     fp64 = None
@@ -512,8 +598,12 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": PREC_NAME[prec],
             "data": "synthetic (seeded water-like MAB model; no dataset)",
             "config": conf,
-            "spectra_per_hour": 3600.0 * value / per_spec,
+            # one spectrum = its ADO-updates at the measured rate plus one equilibration
+            "spectra_per_hour": 3600.0 / (per_spec / value + eq_seconds),
+            "spectra_per_hour_excl_equilibration": 3600.0 * value / per_spec,
+            "equilibration_s": eq_seconds,
             "ado_updates_per_spectrum": per_spec,
+            "error": error,
             "roofline": roof, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
             "fp64_gpu": fp64,
             "gpu_launches": int(launches),
