@@ -97,7 +97,7 @@ def algorithmic_costs(model, d, nado, ado_table, nb_counts, prec):
 # (one ADO of one branch) of one RK4 stage of the tensor-core path: one ncu capture
 # of a 4-branch c3 case, scaled per item (the per-branch working set is the same at
 # 256 branches).  None when the stage kernels have changed since that capture.
-TC_STAGE_TRAFFIC_BYTES_PER_ITEM = 753.4e3
+TC_STAGE_TRAFFIC_BYTES_PER_ITEM = 752.4e3
 
 
 class ClockSampler:
