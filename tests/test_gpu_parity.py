@@ -460,3 +460,26 @@ def test_state_creation_ordered_after_pending_work():
         torch.cuda.synchronize()
         assert np.abs(got[0] - ref[0]).max() < 1e-6 * np.abs(ref).max()
         assert np.abs(got[1] - ref[0]).max() < 1e-6 * np.abs(ref).max()
+
+
+@pytest.mark.gpu
+def test_c5_batch_uneven_sets_against_oracle():
+    """Sets of the seeded c5 batch (levels per mode drawn from {4, 5, 6}, jittered
+    parameters) with uneven basis sizes in one heom_response_2d_batched call, at depth 1
+    and a short grid, against the oracle's response per set."""
+    sets = W.c5_batch()
+    dims = [int(np.prod([md["n_levels"] for md in m["modes"]])) for m in sets]
+    pick = [int(np.argmin(dims)), int(np.argmax(dims))]
+    pick.append(next(i for i in range(len(sets)) if dims[i] not in (dims[pick[0]], dims[pick[1]])))
+    models = [dict(sets[i], depth_L=1) for i in pick]
+    assert len({dims[i] for i in pick}) == 3
+    grid = W.grid(0.25, 2, 3, 3, (0.0, 0.5), t_eq_fs=1.0)
+    hs = [H.heom_build_hierarchy(m) for m in models]
+    eqs = [H.heom_equilibrate(h, grid["dt_fs"], grid["t_eq_fs"], 0.0) for h in hs]
+    RI, RII, SC = H.heom_response_2d_batched(hs, eqs, grid)
+    for i, m in enumerate(models):
+        _, RIo, RIIo, SCo = OH.spectrum_2d(OM.Problem(m), grid)
+        scale = max(np.abs(RIo).max(), np.abs(RIIo).max())
+        assert np.abs(RI[i] - RIo).max() < 1e-10 * scale
+        assert np.abs(RII[i] - RIIo).max() < 1e-10 * scale
+        assert np.abs(SC[i] - SCo).max() < 1e-10 * np.abs(SCo).max()
