@@ -256,8 +256,13 @@ heom_status heom_response_2d_grad(heom_hier *h, const heom_state *rho_eq, const 
  * set is an HEOM_FP64 hierarchy, the sets advance together: each RK4 stage of
  * all sets and all their branches is one kernel launch (per-set models and
  * state pointers in a descriptor table), and each t3 scan is one CUDA-graph
- * replay; results equal those of heom_response_2d per set.  Otherwise the sets
- * run one after the other, each with all its branches batched.
+ * replay.  When every set is an HEOM_TC hierarchy (up to 16 sets), each RK4
+ * stage of the t2 forks and t3 scans of all sets is one tensor-core launch and
+ * one coupling-kernel launch (per-set operators and buffers in the launch's
+ * descriptor; a CTA reloads H' when its next item belongs to another set).  In
+ * both cases results equal those of heom_response_2d per set, bit for bit.
+ * Otherwise the sets run one after the other, each with all its branches
+ * batched.
  */
 heom_status heom_response_2d_batched(heom_hier *const *hs, const heom_state *const *eqs, int n_sets,
                                      const heom_grid *g, double *R_I, double *R_II, double *S_C);

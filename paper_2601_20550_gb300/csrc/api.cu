@@ -227,7 +227,7 @@ void trace_into(heom_hier *h, const typename CxT<R>::type *w, int branches, int 
 
 
 // Original-basis complex128 ADOs -> coupling-basis complex64 (U^T x U), and back.
-static void to_coupling_basis(heom_hier *h, const double2 *x, float2 *out, int64_t elems, cudaStream_t st) {
+void to_coupling_basis(heom_hier *h, const double2 *x, float2 *out, int64_t elems, cudaStream_t st) {
   DeviceBuffer tmp(elems * 16);
   sim_left_kernel<double2><<<grid_for(elems), 256, 0, st>>>(x, (double2 *)tmp.p, h->U64, h->M.d, elems);
   sim_right_kernel<float2><<<grid_for(elems), 256, 0, st>>>((const double2 *)tmp.p, out, h->U64, h->M.d, elems);

@@ -1,5 +1,6 @@
 // Several parameter sets on one grid (heom_response_2d_batched): FP64 sets
-// advance together, one launch per RK4 stage across all sets and branches.
+// advance together, one launch per RK4 stage across all sets and branches;
+// tensor-core sets likewise, one launch pair per stage.
 #include <algorithm>
 #include <cmath>
 #include <complex>
@@ -171,6 +172,101 @@ static void response_2d_multi(heom_hier *const *hs, const heom_state *const *eqs
   CUDA_TRY(cudaStreamSynchronize(st));
 }
 
+// The same schedule for parameter sets built with HEOM_TC (up to 16): the t2
+// forks and the t3 scan of all sets advance together, every RK4 stage one
+// tensor-core launch and one coupling-kernel launch for all sets
+// (tc_rk4_sets); the single-branch t1 trunk of each set runs on the FP32
+// CUDA-core stage, as in response_2d_rows_impl.  Per item the arithmetic is that
+// of the per-set path, so results equal heom_response_2d per set.
+static void response_2d_multi_tc(heom_hier *const *hs, const heom_state *const *eqs, int n_sets, const heom_grid *g,
+                                 const std::vector<double2 *> &Rdev) {
+  cudaStream_t st = hs[0]->stream;
+  const int n1 = g->n1, n3 = g->n3, m = g->steps_per_sample, nt2 = g->n_t2;
+  const double dt = g->dt_fs;
+  std::vector<int> order(nt2);
+  std::vector<int64_t> n2(nt2);
+  for (int i = 0; i < nt2; ++i) {
+    order[i] = i;
+    const double r = g->t2_fs[i] / dt;
+    n2[i] = (int64_t)std::llround(r);
+    if (g->t2_fs[i] < 0 || std::fabs(r - n2[i]) > 1e-6) throw Fail{HEOM_EINVAL, "t2 must be a non-negative multiple of dt"};
+  }
+  std::sort(order.begin(), order.end(), [&](int a, int b) { return n2[a] < n2[b]; });
+  struct TcSetBufs {
+    heom_hier *h;
+    int64_t per;
+    std::unique_ptr<DeviceBuffer> eqR, T, ta, tb, P[4];
+  };
+  std::vector<TcSetBufs> S(n_sets);
+  int64_t sum_per = 0;
+  for (int k = 0; k < n_sets; ++k) {
+    const Model &M = hs[k]->M;
+    S[k].h = hs[k];
+    S[k].per = (int64_t)M.n_ado * M.d * M.d;
+    sum_per += S[k].per;
+    for (auto *b : {&S[k].eqR, &S[k].T, &S[k].ta, &S[k].tb}) b->reset(new DeviceBuffer(S[k].per * 8));
+    to_coupling_basis(hs[k], (const double2 *)eqs[k]->buf.p, (float2 *)S[k].eqR->p, S[k].per, st);
+  }
+  const int nbuf = nt2 > 1 ? 4 : 3;
+  size_t free_b = 0, total_b = 0;
+  CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+  const double budget = 0.85 * (double)free_b;
+  int J = n1;
+  while (J > 1 && (double)nbuf * 2 * J * sum_per * 8 > budget) J = (J + 1) / 2;
+  if ((double)nbuf * 2 * J * sum_per * 8 > budget) throw Fail{HEOM_ENOMEM, "states do not fit in device memory"};
+  for (int k = 0; k < n_sets; ++k) {
+    for (int q = 0; q < 4; ++q)
+      S[k].P[q].reset(new DeviceBuffer(q < nbuf ? (size_t)2 * J * S[k].per * 8 : 16));
+    tc_reserve(hs[k]->tc, (int64_t)2 * J * hs[k]->M.n_ado);
+  }
+  auto bufs = [&](int yq, int aq, int bq, int B) {
+    std::vector<TcRk4Set> v;
+    for (int k = 0; k < n_sets; ++k)
+      v.push_back(TcRk4Set{&hs[k]->tc, (float2 *)S[k].P[yq]->p, (float2 *)S[k].P[aq]->p, (float2 *)S[k].P[bq]->p, B});
+    return v;
+  };
+  for (int j0 = 0; j0 < n1; j0 += J) {
+    const int nj = std::min(J, n1 - j0), B = 2 * nj;
+    const std::vector<TcRk4Set> fork = bufs(0, 1, 2, B), scan = bufs(1, 2, nbuf == 4 ? 3 : 0, B);
+    for (int k = 0; k < n_sets; ++k) {
+      // trunk on the FP32 CUDA-core stage, then the second kick of both pathways
+      heom_hier *h = hs[k];
+      const int64_t per = S[k].per;
+      float2 *T = (float2 *)S[k].T->p;
+      kick_into<float>(h, (const float2 *)S[k].eqR->p, T, 1, 2, st);
+      rk4_steps<float>(h, T, (float2 *)S[k].ta->p, (float2 *)S[k].tb->p, 1, dt, (int64_t)j0 * m, st, HEOM_FP32);
+      float2 *br = (float2 *)S[k].P[0]->p;
+      for (int j = 0; j < nj; ++j) {
+        if (j > 0) rk4_steps<float>(h, T, (float2 *)S[k].ta->p, (float2 *)S[k].tb->p, 1, dt, m, st, HEOM_FP32);
+        kick2_pair_kernel<float><<<grid_for(per), 256, 0, st>>>(T, br + (int64_t)j * per, br + (int64_t)(nj + j) * per,
+                                                               h->mup_vb32, h->mum_vb32, h->M.d, per);
+        count_launch(1);
+        LAUNCH_CHECK();
+      }
+    }
+    int64_t t_now = 0;
+    for (int oi = 0; oi < nt2; ++oi) {
+      const int it = order[oi];
+      tc_rk4_sets(fork, dt, n2[it] - t_now, st);
+      t_now = n2[it];
+      for (int k = 0; k < n_sets; ++k)
+        kick_into<float>(hs[k], (const float2 *)S[k].P[0]->p, (float2 *)S[k].P[1]->p, B, 1, st);
+      GraphCapture cap(st);
+      for (int kk = 0; kk < n3; ++kk) {
+        if (kk > 0) tc_rk4_sets(scan, dt, m, st);
+        for (int k = 0; k < n_sets; ++k)
+          for (int pw = 0; pw < 2; ++pw) {
+            double2 *base = Rdev[k] + (int64_t)it * 2 * n1 * n3 + (int64_t)pw * n1 * n3 + (int64_t)j0 * n3 + kk;
+            trace_into<float>(hs[k], (const float2 *)S[k].P[1]->p + (int64_t)pw * nj * S[k].per, nj, 3, base, n3, st);
+          }
+      }
+      cap.replay();
+    }
+  }
+  CUDA_TRY(cudaStreamSynchronize(st));
+  for (int k = 0; k < n_sets; ++k) check_tc_error(hs[k]);
+}
+
 }  // namespace heom
 
 extern "C" {
@@ -179,13 +275,14 @@ heom_status heom_response_2d_batched(heom_hier *const *hs, const heom_state *con
                                      const heom_grid *g, double *R_I, double *R_II, double *S_C) {
   if (!hs || !eqs || !g || n_sets < 1) return fail(HEOM_EINVAL, "bad batched arguments");
   const size_t blk = (size_t)g->n_t2 * g->n1 * g->n3;
-  bool one_launch = n_sets > 1;
+  bool all64 = n_sets > 1, alltc = n_sets > 1 && n_sets <= 16;
   for (int i = 0; i < n_sets; ++i) {
     heom_status a = check_response_args(hs[i], eqs[i], g);
     if (a != HEOM_OK) return a;
-    one_launch = one_launch && hs[i]->M.precision == HEOM_FP64;
+    all64 = all64 && hs[i]->M.precision == HEOM_FP64;
+    alltc = alltc && hs[i]->M.precision == HEOM_TC;
   }
-  if (!one_launch) {
+  if (!all64 && !alltc) {
     for (int i = 0; i < n_sets; ++i) {
       heom_status st = heom_response_2d(hs[i], eqs[i], g, R_I ? R_I + i * blk * 2 : nullptr,
                                         R_II ? R_II + i * blk * 2 : nullptr, S_C ? S_C + i * blk : nullptr);
@@ -205,7 +302,13 @@ heom_status heom_response_2d_batched(heom_hier *const *hs, const heom_state *con
     CUDA_TRY(cudaMemsetAsync(Rall.p, 0, Rall.bytes, st));
     std::vector<double2 *> Rdev(n_sets);
     for (int i = 0; i < n_sets; ++i) Rdev[i] = (double2 *)Rall.p + (size_t)i * nt2 * 2 * one;
-    response_2d_multi(hs, eqs, n_sets, g, Rdev);
+    if (alltc) {
+      for (int i = 0; i < n_sets; ++i)
+        if (!tc_supported(hs[i]->tc)) throw Fail{HEOM_EINVAL, "tensor-core path not prepared for this hierarchy"};
+      response_2d_multi_tc(hs, eqs, n_sets, g, Rdev);
+    } else {
+      response_2d_multi(hs, eqs, n_sets, g, Rdev);
+    }
     const double dtau = g->dt_fs * g->steps_per_sample;
     for (int i = 0; i < n_sets; ++i)
       for (int it = 0; it < nt2; ++it) {

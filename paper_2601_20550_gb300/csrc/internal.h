@@ -233,6 +233,8 @@ struct GraphCapture {
 
 // Raises HEOM_ETIMEOUT if a tensor-core stage wait ran out.
 void check_tc_error(heom_hier *h);
+// Product-basis complex128 ADOs -> coupling-basis complex64 (U^T x U U); synchronises st.
+void to_coupling_basis(heom_hier *h, const double2 *x, float2 *out, int64_t elems, cudaStream_t st);
 // Rows [jr0, jr1) of R_I and R_II into Rdev laid out [n_t2][2][jr1 - jr0][n3].
 template <typename R>
 void response_2d_rows_impl(heom_hier *h, const heom_state *eq, const heom_grid *g, int jr0, int jr1,

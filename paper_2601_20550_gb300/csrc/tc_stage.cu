@@ -40,6 +40,7 @@ namespace {
 
 constexpr int kThreads = 544;
 constexpr int kTcMaxModes = 4;
+constexpr int kTcMaxSets = 16;
 constexpr uint32_t kHTile = 32768;               // 128 x 128 FP16
 constexpr uint32_t kZZ = 65536;                  // 256 x 128 FP16 (re | im rows)
 constexpr uint32_t kTiles = 2 * kZZ + 3 * kHTile;
@@ -48,7 +49,10 @@ constexpr uint32_t kTmemCols = 512;             // two accumulator buffers of 25
 constexpr int kProducers = 384;                  // warps 0-11
 constexpr int kEpilogue = 128;                   // warps 12-15
 constexpr int kMmaWarp = 16;                     // warp 16: tensor-core issue
-constexpr int kProdRows = 12;                    // rows per producer batch (2 batches cover 144 >= 128 rows)
+// Rows of w_n per producer thread: 24 (6 row groups x 24 = 144 >= 128 rows), loaded
+// in 3 batches of 8 (with the hi parts of all 24 held until the tiles are free, a
+// batch of 12 exceeds the 96-register budget of a 17-warp CTA and spills).
+constexpr int kProdSlots = 24;
 static_assert(kProducers + kEpilogue + 32 == kThreads, "warp roles");
 // Bounded waits: a wait gives up after the hierarchy's time limit (globaltimer,
 // checked at the second poll and then every 256 polls) or after kWaitPolls
@@ -58,16 +62,40 @@ constexpr long kWaitPolls = 1L << 30;
 // limit, independent of the (possibly shortened) wait limit.
 constexpr uint64_t kDrainNs = 2000000000ull;
 
-struct TcArgs {
-  const float2 *w;
-  const float2 *y;
-  float2 *out;
-  float alpha;
-  int64_t n_items;
-  const unsigned *max_in;   // per item: largest |component| of w (float bits)
-  unsigned *max_out;        // per item: running max |component| of out
-  TcOperators ops;
+// One parameter set of a stage launch: its operators and this stage's buffers.
+// A launch covers up to kTcMaxSets sets (hierarchies of any basis size up to
+// 128); their work items are concatenated, set after set.
+struct TcSet {
+  const uint4 *himg;          // shared-memory images of the H' pieces
+  const float *lam;           // [n_modes][128] lam_s[digit_s(a)]
+  const double *decay;        // [n_ado]
+  const int *nb_off, *nb_idx; // coupling lists
+  const float *nb_cA, *nb_cB;
+  const float2 *w, *y;        // stage input and step-start state
+  float2 *out, *tpart;        // stage output; tensor-core part (may equal out, not w or y)
+  const unsigned *max_in;     // per item: largest |component| of w (float bits)
+  unsigned *max_out;          // per item: running max |component| of out
+  int64_t item_begin;         // first work item of the set in the launch
+  int64_t vt_begin;           // first block of the set in the coupling kernel's grid
+  float inv_sh;               // 1 / (power-of-two scale applied to H')
+  int d, n_ado, n_modes, bands;
 };
+
+struct TcArgs {
+  TcSet sets[kTcMaxSets];
+  int n_sets, n_hpieces;
+  int64_t n_items;            // work items of all sets
+  float alpha;
+  int *err;                   // device error word (bounded waits)
+  uint64_t wait_ns;           // time limit of each wait
+};
+
+// Set of a work item (items are concatenated set after set).
+__device__ __forceinline__ int set_of_item(const TcArgs &P, int64_t item) {
+  int k = 0;
+  while (k + 1 < P.n_sets && item >= P.sets[k + 1].item_begin) ++k;
+  return k;
+}
 
 __host__ __device__ inline uint32_t sw128_offset(int r, int c, uint32_t colblock_stride) {
   const int j = c >> 6, cc = c & 63;
@@ -216,20 +244,25 @@ __device__ __forceinline__ float item_scale(unsigned mbits) {
 //   warps 12-15 (epilogue): per item, wait for the MMAs, read the accumulator,
 //              store tpart and release the buffer.
 // The epilogue of item k overlaps the MMAs of item k + 1 and the loads of k + 2.
-__global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
+template <bool kMulti>
+__global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(const __grid_constant__ TcArgs P) {
+  constexpr int kProdRows = 8;                             // rows per producer batch
+  constexpr int kProdBatches = kProdSlots / kProdRows;
   extern __shared__ uint8_t smem_raw[];
   __shared__ uint64_t bar_mma[2], bar_lo[2], bar_full[2], bar_epi[2], bar_ready_hi[2], bar_ready_lo[2];
   __shared__ uint32_t tmem_base;
   __shared__ int s_abort;
 
-  const TcOperators &op = P.ops;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t *base = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
   uint8_t *ZZ1 = base, *ZZ2 = base + kZZ, *HT = base + 2 * kZZ;
 
+  // tiles zeroed (rows and columns past d stay zero) and the H' pieces of the set
+  // of this CTA's first item
+  const int first_set = kMulti && (int64_t)blockIdx.x < P.n_items ? set_of_item(P, blockIdx.x) : 0;
   for (uint32_t i = tid; i < 2 * kZZ / 16; i += kThreads) reinterpret_cast<uint4 *>(base)[i] = make_uint4(0, 0, 0, 0);
-  for (uint32_t i = tid; i < (uint32_t)op.n_hpieces * kHTile / 16; i += kThreads)
-    reinterpret_cast<uint4 *>(HT)[i] = op.himg[i];
+  for (uint32_t i = tid; i < (uint32_t)P.n_hpieces * kHTile / 16; i += kThreads)
+    reinterpret_cast<uint4 *>(HT)[i] = P.sets[first_set].himg[i];
   if (tid == 0) {
     s_abort = 0;
     for (int t = 0; t < 2; ++t) {
@@ -252,8 +285,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_base;
 
-  const int d = op.d;
-  const int64_t dd = (int64_t)d * d;
   const int64_t n_mine = P.n_items > blockIdx.x ? (P.n_items - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
   if (tid < kProducers) {
@@ -261,7 +292,6 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
     const int cp = tid & 63;           // column pair: columns 2cp, 2cp + 1
     const int r0 = tid >> 6;           // first row; rows r0, r0 + 6, ...
     const int c = 2 * cp;
-    const bool active = c < d;
     // byte offsets of this thread's __half2 in the 128B-swizzled tiles: row a of a
     // 64-column block sits at 128 a, its 16-byte chunk (c mod 64) / 8 is XORed with
     // a mod 8.  Rows a = r0 + 6 g repeat a mod 8 every 4 steps of g (6 * 4 = 24),
@@ -274,15 +304,26 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       row_ofs[u] = (uint32_t)(c >> 6) * (kZZ / 2) + (uint32_t)a * 128u +
                    ((uint32_t)((cc >> 3) ^ (a & 7)) << 4) + (uint32_t)((cc * 2) & 15);
     }
+    int prev_set = first_set;
     for (int64_t k = 0; k < n_mine; ++k) {
       const int64_t item = blockIdx.x + k * gridDim.x;
       const int t = (int)(k & 1);
-      const float2 *wn = P.w + item * dd;
+      const int ks = kMulti ? set_of_item(P, item) : 0;
+      const TcSet &S = P.sets[ks];
+      const int d = S.d;
+      const int64_t dd = (int64_t)d * d, li = item - S.item_begin;
+      const bool active = c < d;
+      const float2 *wn = S.w + li * dd;
       // warm L2 with the next item's w_n while this one is converted (one bulk prefetch)
-      if (k + 1 < n_mine && tid == 0) l2_prefetch_bulk(P.w + (item + gridDim.x) * dd, dd * 8);
+      if (k + 1 < n_mine && tid == 0) {
+        const int64_t nx = item + gridDim.x;
+        const TcSet &SN = P.sets[kMulti ? set_of_item(P, nx) : 0];
+        const int64_t ddn = (int64_t)SN.d * SN.d;
+        l2_prefetch_bulk(SN.w + (nx - SN.item_begin) * ddn, ddn * 8);
+      }
       // The first batch of w_n is loaded before the wait, so its latency overlaps
       // the previous item's first MMA group.
-      float2 v[2 * kProdRows];
+      float2 v[2 * kProdRows];   // one batch: kProdRows rows x 2 columns
       auto load_batch = [&](int bt) {
         const int ab = r0 + 6 * kProdRows * bt;
 #pragma unroll
@@ -294,18 +335,35 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       };
       load_batch(0);
       // power-of-two scale from the item's largest component (kept by the previous stage)
-      const float scale = item_scale(P.max_in[item]);
+      const float scale = item_scale(S.max_in[li]);
       // The lo tiles are free once the previous item's first MMA (H1 Z2) has
       // completed; every producer takes the same decision to go on or to leave.
-      if (k >= 1) mbar_wait(&bar_lo[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort, op.wait_ns);
+      // An item of another parameter set than the previous one waits for all of
+      // the previous item's MMAs (they read H'), then the producers load the new
+      // set's H' pieces and clear the tiles (its basis may be smaller).
+      const bool new_set = kMulti && ks != prev_set;
+      prev_set = ks;
+      if (k >= 1) {
+        if (new_set)
+          mbar_wait(&bar_mma[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), P.err, &s_abort, P.wait_ns);
+        else
+          mbar_wait(&bar_lo[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), P.err, &s_abort, P.wait_ns);
+      }
       if (producer_sync_any(*(volatile int *)&s_abort != 0)) break;
+      if (new_set) {
+        for (uint32_t i = tid; i < 2 * kZZ / 16; i += kProducers)
+          reinterpret_cast<uint4 *>(base)[i] = make_uint4(0, 0, 0, 0);
+        for (uint32_t i = tid; i < (uint32_t)P.n_hpieces * kHTile / 16; i += kProducers)
+          reinterpret_cast<uint4 *>(HT)[i] = S.himg[i];
+        producer_sync_any(false);   // cleared before any producer writes its tile parts
+      }
       // scale and split into FP16 hi + lo; lo goes to the tiles now (the MMA warp
       // starts this item with H1 Z2 as soon as they are all written), hi is kept in
       // registers until the previous item's MMAs have all completed
-      __half2 hre[2 * kProdRows], him[2 * kProdRows];
+      __half2 hre[kProdSlots], him[kProdSlots];
 #pragma unroll
-      for (int bt = 0; bt < 2; ++bt) {
-        if (bt == 1) load_batch(1);
+      for (int bt = 0; bt < kProdBatches; ++bt) {
+        if (bt > 0) load_batch(bt);
 #pragma unroll
         for (int i = 0; i < kProdRows; ++i) {
           const int g = kProdRows * bt + i;                  // row a = r0 + 6 g
@@ -315,11 +373,11 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
           him[g] = __float22half2_rn(xi);
           const float2 fr = __half22float2(hre[g]), fi = __half22float2(him[g]);
           const __half2 lr = __float22half2_rn(make_float2(xr.x - fr.x, xr.y - fr.y));
-          const __half2 li = __float22half2_rn(make_float2(xi.x - fi.x, xi.y - fi.y));
+          const __half2 lim = __float22half2_rn(make_float2(xi.x - fi.x, xi.y - fi.y));
           if (active && r0 + 6 * g < d) {
             const uint32_t o = row_ofs[g & 3] + 3072u * (uint32_t)(g >> 2);
             *reinterpret_cast<__half2 *>(ZZ2 + o) = lr;
-            *reinterpret_cast<__half2 *>(ZZ2 + o + 16384u) = li;
+            *reinterpret_cast<__half2 *>(ZZ2 + o + 16384u) = lim;
           }
         }
       }
@@ -327,10 +385,10 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&bar_ready_lo[t]);
       // the hi tiles are free once the previous item's MMAs have all completed
-      if (k >= 1) mbar_wait(&bar_mma[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), op.err, &s_abort, op.wait_ns);
+      if (k >= 1) mbar_wait(&bar_mma[(k - 1) & 1], (uint32_t)(((k - 1) >> 1) & 1), P.err, &s_abort, P.wait_ns);
       if (active) {
 #pragma unroll
-        for (int g = 0; g < 2 * kProdRows; ++g)
+        for (int g = 0; g < kProdSlots; ++g)
           if (r0 + 6 * g < d) {
             const uint32_t o = row_ofs[g & 3] + 3072u * (uint32_t)(g >> 2);
             *reinterpret_cast<__half2 *>(ZZ1 + o) = hre[g];
@@ -350,14 +408,17 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       const int64_t item = blockIdx.x + k * gridDim.x;
       const int t = (int)(k & 1);
       const uint32_t par = (uint32_t)((k >> 1) & 1);
-      bool ok = mbar_wait(&bar_full[t], par, op.err, &s_abort, op.wait_ns);
-      ok = ok && mbar_wait(&bar_mma[t], par, op.err, &s_abort, op.wait_ns);
+      bool ok = mbar_wait(&bar_full[t], par, P.err, &s_abort, P.wait_ns);
+      ok = ok && mbar_wait(&bar_mma[t], par, P.err, &s_abort, P.wait_ns);
       if (!__all_sync(0xffffffffu, ok)) break;
       asm volatile("tcgen05.fence::after_thread_sync;");
       // tpart = alpha (-i C); the streaming kernel adds y and the rest next
-      if (tid == kProducers) P.max_out[item] = 0u;
-      const float sc = P.alpha * op.inv_sh / item_scale(P.max_in[item]);
-      float2 *ob = P.out + item * dd;
+      const TcSet &S = P.sets[kMulti ? set_of_item(P, item) : 0];
+      const int d = S.d;
+      const int64_t dd = (int64_t)d * d, li = item - S.item_begin;
+      if (tid == kProducers) S.max_out[li] = 0u;
+      const float sc = P.alpha * S.inv_sh / item_scale(S.max_in[li]);
+      float2 *ob = S.tpart + li * dd;
       const uint32_t tcol = tmem + lane_field + (uint32_t)t * 256u;
       for (int a0 = 0; a0 < d; a0 += 16) {
         uint32_t rr[16], ri[16];
@@ -384,7 +445,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       const uint32_t hh = smem_u32(HT);
       const uint32_t id_neg = idesc(128, 256, 0, 0, 1);
       const uint32_t id_mn = idesc(128, 128, 1, 0, 0);
-      const int nh = op.n_hpieces;
+      const int nh = P.n_hpieces;
       // the mbarrier phase of the most recent commit (bar_lo[t] as 2 t, bar_mma[t]
       // as 2 t + 1; -1 none): every MMA issued before it has completed once that
       // phase completes
@@ -394,8 +455,8 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
         const int t = (int)(k & 1);
         // the tiles of item k are written; its accumulator buffer is free once
         // the epilogue of item k - 2 released it
-        bool ok = mbar_wait(&bar_ready_lo[t], (uint32_t)((k >> 1) & 1), op.err, &s_abort, op.wait_ns);
-        ok = ok && (k < 2 || mbar_wait(&bar_epi[t], (uint32_t)(((k - 2) >> 1) & 1), op.err, &s_abort, op.wait_ns));
+        bool ok = mbar_wait(&bar_ready_lo[t], (uint32_t)((k >> 1) & 1), P.err, &s_abort, P.wait_ns);
+        ok = ok && (k < 2 || mbar_wait(&bar_epi[t], (uint32_t)(((k - 2) >> 1) & 1), P.err, &s_abort, P.wait_ns));
         if (!ok) break;
         // Products kept by the split, the small ones first: H1 Z2 (lo tiles, group
         // 0, committed on its own so the producers can refill the lo tiles), then
@@ -409,7 +470,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
         const uint32_t dcol = tmem + (uint32_t)t * 256u;
         for (int grp = 0; grp < 2; ++grp) {
           if (grp == 1) {
-            if (!mbar_wait(&bar_ready_hi[t], (uint32_t)((k >> 1) & 1), op.err, &s_abort, op.wait_ns)) break;
+            if (!mbar_wait(&bar_ready_hi[t], (uint32_t)((k >> 1) & 1), P.err, &s_abort, P.wait_ns)) break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;");
           const int np = grp == 0 ? 1 : nh;
@@ -438,7 +499,7 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(TcArgs P) {
       // drain, on the normal and on the abort path: every committed MMA must
       // complete before the tiles and the tensor memory go away
       if (last_bar >= 0)
-        mbar_drain((last_bar & 1) ? &bar_mma[last_bar >> 1] : &bar_lo[last_bar >> 1], last_par, op.err);
+        mbar_drain((last_bar & 1) ? &bar_mma[last_bar >> 1] : &bar_lo[last_bar >> 1], last_par, P.err);
     }
     __syncwarp();
   }
@@ -463,16 +524,19 @@ constexpr int kVtRowsPerThread = 8;
 constexpr int kVtRows = 2 * kVtRowsPerThread;
 constexpr int kMaxNb = 32;
 
-__global__ void __launch_bounds__(kVtThreads) vterm_kernel(const float2 *__restrict__ w, const float2 *y,
-                                                          const float2 *tpart, float2 *out, float alpha,
-                                                          TcOperators op, int bands, unsigned *max_out) {
-  const int d = op.d, nm = op.n_modes;
+__global__ void __launch_bounds__(kVtThreads) vterm_kernel(const __grid_constant__ TcArgs P) {
+  int ks = 0;   // the parameter set of this block (blocks are concatenated set after set)
+  while (ks + 1 < P.n_sets && (int64_t)blockIdx.x >= P.sets[ks + 1].vt_begin) ++ks;
+  const TcSet &S = P.sets[ks];
+  const int d = S.d, nm = S.n_modes, bands = S.bands;
   const int64_t dd = (int64_t)d * d;
-  const int64_t item = blockIdx.x / bands;
-  const int band = blockIdx.x - (int)(item * bands);
-  const int n = (int)(item % op.n_ado);
-  const int64_t br = item / op.n_ado;
-  const float2 *wb = w + br * op.n_ado * dd;
+  const int64_t lb = (int64_t)blockIdx.x - S.vt_begin;
+  const int64_t item = lb / bands;   // item within the set
+  const int band = (int)(lb - item * bands);
+  const int n = (int)(item % S.n_ado);
+  const int64_t br = item / S.n_ado;
+  const float2 *wb = S.w + br * S.n_ado * dd;
+  const float alpha = P.alpha;
   const int b = threadIdx.x & 127, par = threadIdx.x >> 7;
   const int a0 = band * kVtRows + par;          // rows a0, a0 + 2, ..., a0 + 14
   // lanes past the last column keep running (no loads or stores) so that the
@@ -482,22 +546,22 @@ __global__ void __launch_bounds__(kVtThreads) vterm_kernel(const float2 *__restr
   float re[kVtRowsPerThread], im[kVtRowsPerThread];
 #pragma unroll
   for (int j = 0; j < kVtRowsPerThread; ++j) re[j] = im[j] = 0.f;
-  const int *off = op.nb_off + n * nm;
+  const int *off = S.nb_off + n * nm;
   for (int s = 0; s < nm; ++s) {
     const int lo = off[s], hi = off[s + 1];
     if (lo == hi) continue;
-    const float lb = op.lam[s * 128 + b];
+    const float lb = S.lam[s * 128 + b];
     float f[kVtRowsPerThread], g[kVtRowsPerThread];
 #pragma unroll
     for (int j = 0; j < kVtRowsPerThread; ++j) {
       const int a = min(a0 + 2 * j, d - 1);
-      const float la = op.lam[s * 128 + a];
+      const float la = S.lam[s * 128 + a];
       f[j] = la - lb;
       g[j] = la + lb;
     }
     for (int q = lo; q < hi; ++q) {
-      const float2 *wm = wb + (int64_t)op.nb_idx[q] * dd + e0;
-      const float cA = op.nb_cA[q], cB = op.nb_cB[q];
+      const float2 *wm = wb + (int64_t)S.nb_idx[q] * dd + e0;
+      const float cA = S.nb_cA[q], cB = S.nb_cB[q];
       float2 x[kVtRowsPerThread];
 #pragma unroll
       for (int j = 0; j < kVtRowsPerThread; ++j) x[j] = j < nrow ? wm[j * es] : make_float2(0.f, 0.f);
@@ -510,7 +574,7 @@ __global__ void __launch_bounds__(kVtThreads) vterm_kernel(const float2 *__restr
     }
   }
   {  // decay: - gamma_n w_n
-    const float dec = (float)op.decay[n];
+    const float dec = (float)S.decay[n];
     const float2 *wn = wb + (int64_t)n * dd + e0;
     float2 x[kVtRowsPerThread];
 #pragma unroll
@@ -521,9 +585,9 @@ __global__ void __launch_bounds__(kVtThreads) vterm_kernel(const float2 *__restr
       im[j] -= dec * x[j].y;
     }
   }
-  const float2 *yb = y + item * dd + e0;
-  const float2 *tb = tpart + item * dd + e0;
-  float2 *ob = out + item * dd + e0;
+  const float2 *yb = S.y + item * dd + e0;
+  const float2 *tb = S.tpart + item * dd + e0;
+  float2 *ob = S.out + item * dd + e0;
   float2 yv[kVtRowsPerThread], tv[kVtRowsPerThread];
 #pragma unroll
   for (int j = 0; j < kVtRowsPerThread; ++j) {
@@ -541,7 +605,7 @@ __global__ void __launch_bounds__(kVtThreads) vterm_kernel(const float2 *__restr
   // running max |out| of the item (the tensor-core kernel cleared it)
 #pragma unroll
   for (int o2 = 16; o2 > 0; o2 >>= 1) omax = fmaxf(omax, __shfl_xor_sync(0xffffffffu, omax, o2));
-  if ((threadIdx.x & 31) == 0 && max_out) atomicMax(max_out + item, __float_as_uint(omax));
+  if ((threadIdx.x & 31) == 0 && S.max_out) atomicMax(S.max_out + item, __float_as_uint(omax));
 }
 
 // Largest component magnitude of every item of a state (bit pattern of a
@@ -637,29 +701,73 @@ void tc_build(TcOperators &tc, const Model &M, const VbModel &vb, std::vector<vo
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&tc.sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaFuncSetAttribute(tc_stage_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn) != cudaSuccess)
+  if (cudaFuncSetAttribute(tc_stage_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(tc_stage_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemDyn) != cudaSuccess)
     throw std::invalid_argument("cannot reserve shared memory for the tensor-core stage");
   tc.ready = true;
 }
 
 bool tc_supported(const TcOperators &tc) { return tc.ready; }
 
-void tc_stage(const TcOperators &tc, const float2 *w, const float2 *y, float2 *out, float2 *tpart, int branches,
-              float alpha, const unsigned *max_in, unsigned *max_out, cudaStream_t st) {
-  const int64_t n_items = (int64_t)branches * tc.n_ado;
+// One RK4 stage, out = y + alpha L(w), of every set: one tensor-core launch and
+// one coupling-kernel launch for all of them.  which = 0..3 selects the Horner
+// stage's buffers (w, out, tpart, max_in, max_out) of each set.
+static void tc_stage_sets(const std::vector<TcRk4Set> &sets, int which, float alpha, cudaStream_t st) {
   TcArgs a;
-  a.w = w;
-  a.y = y;
-  a.out = tpart;   // alpha * (-i [H', w]) goes to tpart first
+  std::memset(&a, 0, sizeof a);
+  a.n_sets = (int)sets.size();
   a.alpha = alpha;
-  a.n_items = n_items;
-  a.max_in = max_in;
-  a.max_out = max_out;
-  a.ops = tc;
-  const int grid = (int)std::min<int64_t>(n_items, tc.sms);
-  tc_stage_kernel<<<grid, kThreads, kSmemDyn, st>>>(a);
-  const int bands = (tc.d + kVtRows - 1) / kVtRows;   // 16-row bands
-  vterm_kernel<<<(unsigned)(n_items * bands), kVtThreads, 0, st>>>(w, y, tpart, out, alpha, tc, bands, max_out);
+  a.n_hpieces = sets[0].tc->n_hpieces;
+  a.err = sets[0].tc->err;
+  a.wait_ns = sets[0].tc->wait_ns;
+  int64_t items = 0, blocks = 0;
+  for (int k = 0; k < a.n_sets; ++k) {
+    const TcRk4Set &R = sets[k];
+    const TcOperators &tc = *R.tc;
+    TcSet &S = a.sets[k];
+    unsigned *my = tc.maxbuf, *ma = tc.maxbuf + tc.max_items, *mb = tc.maxbuf + 2 * tc.max_items;
+    // stage buffers of the nested (Horner) form; the tensor-core part goes to a
+    // buffer that is neither y nor w: out itself in stages 1-3, the free scratch wb
+    // in stage 4 (out = y there)
+    const float2 *w[4] = {R.y, R.wa, R.wb, R.wa};
+    float2 *out[4] = {R.wa, R.wb, R.wa, R.y};
+    float2 *tp[4] = {R.wa, R.wb, R.wa, R.wb};
+    const unsigned *mi[4] = {my, ma, mb, ma};
+    unsigned *mo[4] = {ma, mb, ma, my};
+    S.himg = tc.himg;
+    S.lam = tc.lam;
+    S.decay = tc.decay;
+    S.nb_off = tc.nb_off;
+    S.nb_idx = tc.nb_idx;
+    S.nb_cA = tc.nb_cA;
+    S.nb_cB = tc.nb_cB;
+    S.w = w[which];
+    S.y = R.y;
+    S.out = out[which];
+    S.tpart = tp[which];
+    S.max_in = mi[which];
+    S.max_out = mo[which];
+    S.inv_sh = tc.inv_sh;
+    S.d = tc.d;
+    S.n_ado = tc.n_ado;
+    S.n_modes = tc.n_modes;
+    S.bands = (tc.d + kVtRows - 1) / kVtRows;   // 16-row bands
+    S.item_begin = items;
+    S.vt_begin = blocks;
+    const int64_t n = (int64_t)R.branches * tc.n_ado;
+    items += n;
+    blocks += n * S.bands;
+  }
+  a.n_items = items;
+  if (items == 0) return;
+  if (blocks > 0x7fffffffLL) throw std::invalid_argument("too many work items for one stage launch");
+  const int grid = (int)std::min<int64_t>(items, sets[0].tc->sms);
+  if (a.n_sets > 1)
+    tc_stage_kernel<true><<<grid, kThreads, kSmemDyn, st>>>(a);
+  else
+    tc_stage_kernel<false><<<grid, kThreads, kSmemDyn, st>>>(a);
+  vterm_kernel<<<(unsigned)blocks, kVtThreads, 0, st>>>(a);
   count_launch(2);
 }
 
@@ -672,22 +780,30 @@ void tc_reserve(TcOperators &tc, int64_t n_items) {
   tc.max_items = n_items;
 }
 
+void tc_rk4_sets(const std::vector<TcRk4Set> &sets, double dt, int64_t nsteps, cudaStream_t st) {
+  if (sets.empty() || nsteps <= 0) return;
+  if ((int)sets.size() > kTcMaxSets) throw std::invalid_argument("too many parameter sets for one stage launch");
+  bool any = false;
+  for (const TcRk4Set &R : sets) {
+    const int64_t n_items = (int64_t)R.branches * R.tc->n_ado;
+    if (n_items <= 0) continue;
+    any = true;
+    tc_reserve(*R.tc, n_items);
+    item_max_kernel<<<(unsigned)n_items, 256, 0, st>>>(R.y, (int64_t)R.tc->d * R.tc->d, R.tc->maxbuf);
+    count_launch(1);
+  }
+  if (!any) return;
+  for (int64_t s = 0; s < nsteps; ++s) {
+    tc_stage_sets(sets, 0, (float)(dt / 4), st);
+    tc_stage_sets(sets, 1, (float)(dt / 3), st);
+    tc_stage_sets(sets, 2, (float)(dt / 2), st);
+    tc_stage_sets(sets, 3, (float)dt, st);
+  }
+}
+
 void tc_rk4_steps(TcOperators &tc, float2 *y, float2 *wa, float2 *wb, int branches, double dt, int64_t nsteps,
                   cudaStream_t st) {
-  const int64_t n_items = (int64_t)branches * tc.n_ado;
-  if (n_items <= 0 || nsteps <= 0) return;
-  tc_reserve(tc, n_items);
-  unsigned *my = tc.maxbuf, *ma = tc.maxbuf + tc.max_items, *mb = tc.maxbuf + 2 * tc.max_items;
-  item_max_kernel<<<(unsigned)n_items, 256, 0, st>>>(y, (int64_t)tc.d * tc.d, my);
-  count_launch(1);
-  for (int64_t s = 0; s < nsteps; ++s) {
-    // the tensor-core part of a stage goes to a buffer that is neither y nor w:
-    // out itself in stages 1-3, the free scratch wb in stage 4 (out = y there)
-    tc_stage(tc, y, y, wa, wa, branches, (float)(dt / 4), my, ma, st);
-    tc_stage(tc, wa, y, wb, wb, branches, (float)(dt / 3), ma, mb, st);
-    tc_stage(tc, wb, y, wa, wa, branches, (float)(dt / 2), mb, ma, st);
-    tc_stage(tc, wa, y, y, wb, branches, (float)dt, ma, my, st);
-  }
+  tc_rk4_sets({TcRk4Set{&tc, y, wa, wb, branches}}, dt, nsteps, st);
 }
 
 }  // namespace heom

@@ -53,11 +53,19 @@ void tc_rk4_steps(TcOperators &tc, float2 *y, float2 *wa, float2 *wb, int branch
                   int64_t nsteps, cudaStream_t st);
 // Grow the per-item maxima workspace to n_items (outside any stream capture).
 void tc_reserve(TcOperators &tc, int64_t n_items);
-// One stage out = y + alpha L(w): the tensor-core kernel writes
-// tpart = alpha (-i [H', w]) (tpart may equal out but not y or w), then the
-// streaming kernel writes out = y + tpart + alpha (-gamma w + sum kappa w_nb).
-// max_in holds the per-item max |w|; max_out receives max |out|.
-void tc_stage(const TcOperators &tc, const float2 *w, const float2 *y, float2 *out, float2 *tpart, int branches,
-              float alpha, const unsigned *max_in, unsigned *max_out, cudaStream_t st);
+// Buffers of one parameter set for tc_rk4_sets: the state y and two scratch
+// states, each [branches][n_ado][d][d] complex64 in the coupling basis.
+struct TcRk4Set {
+  TcOperators *tc;
+  float2 *y, *wa, *wb;
+  int branches;
+};
+// n RK4 steps (Horner form) of several parameter sets (up to 16, hierarchies built
+// with HEOM_TC, any basis size up to 128) together: every stage of all sets is one
+// tensor-core launch and one coupling-kernel launch.  Each stage writes
+// tpart = alpha (-i [H', w]) (the tensor-core kernel), then out = y + tpart +
+// alpha (-gamma w + sum kappa w_nb) (the coupling kernel).  Per item the
+// arithmetic does not depend on the other sets, so results equal per-set calls.
+void tc_rk4_sets(const std::vector<TcRk4Set> &sets, double dt, int64_t nsteps, cudaStream_t st);
 
 }  // namespace heom

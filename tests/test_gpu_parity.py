@@ -344,14 +344,29 @@ def test_batched_one_launch_equals_per_set():
 
 
 @pytest.mark.gpu
-def test_batched_mixed_precision_sets_fall_back():
-    grid = W.grid(0.5, 4, 6, 6, (0.0,), t_eq_fs=20.0)
-    models = [W.small_three_mode(n=3, depth_L=2), W.small_three_mode(n=2, depth_L=2)]
+def test_batched_tensor_core_sets_one_launch():
+    """Three tensor-core parameter sets of different basis size advance together (one
+    tensor-core and one coupling-kernel launch per RK4 stage for all sets): the results
+    equal the per-set calls bit for bit and the oracle within the mixed-path tolerance."""
+    grid = W.grid(0.5, 4, 6, 5, (0.0, 2.0), t_eq_fs=20.0)
+    models = [W.small_three_mode(n=3, depth_L=2), W.small_three_mode(n=2, depth_L=2),
+              W.small_two_mode(n1=4, n2=3, depth_L=3)]
     hs = [H.heom_build_hierarchy(m, H.TC) for m in models]
-    eqs = [H.heom_equilibrate(h, 0.5, 20.0, 0.0) for h in hs]
+    assert len({h.d for h in hs}) == 3
+    eqs = [H.heom_equilibrate(h, grid["dt_fs"], grid["t_eq_fs"], 0.0) for h in hs]
+    n0 = H.heom_launch_count()
     RI, RII, SC = H.heom_response_2d_batched(hs, eqs, grid)
+    launches_batched = H.heom_launch_count() - n0
+    n0 = H.heom_launch_count()
+    for i, (h, eq) in enumerate(zip(hs, eqs)):
+        ri, rii, sc = H.heom_response_2d(h, eq, grid)
+        assert np.array_equal(RI[i], ri) and np.array_equal(RII[i], rii) and np.array_equal(SC[i], sc)
+    launches_single = H.heom_launch_count() - n0
+    assert launches_batched < launches_single
     for i, m in enumerate(models):
         _, RIo, RIIo, SCo = OH.spectrum_2d(OM.Problem(m), grid)
+        scale = max(np.abs(RIo).max(), np.abs(RIIo).max())
+        assert np.abs(RI[i] - RIo).max() < 1e-4 * scale
         assert np.abs(SC[i] - SCo).max() < 1e-4 * np.abs(SCo).max()
 
 
