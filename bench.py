@@ -487,6 +487,13 @@ def main():
                 "frac_nested_form": achieved * (11.0 / 20.0) / peak,
                 "nested_form_bytes_per_ado_update": bytes_upd * 11.0 / 20.0,
                 "flops_TFLOPs": flops_upd * per_launch_units / stage_s / 1e12}
+        if prec == 2:
+            # the coupling kernel's launch shape the autotuner chose for this batch
+            tuned = [e for e in H.heom_get_tuning(h) if e[0] == 2 and e[1] == B * nado * d * d]
+            if tuned:
+                bands = tuned[0][3] // (B * nado)
+                roof["coupling_kernel_shape"] = {"threads": tuned[0][2], "blocks": tuned[0][3],
+                                                 "rows_per_block": -(-d // bands)}
 
     # ---------------- error against the FP64 path ----------------
     # (a) the timed traces: every branch of the timed batch started from the same

@@ -218,9 +218,17 @@ heom_status heom_steady_state(heom_hier *h, double tol, int restart, int max_ite
  * a tuning aid).  The first RK4 propagation of a given size on the FP64
  * (kind 0) or FP32 coupling-basis (kind 1) path times nine launch shapes of its
  * stage kernel (64/128/256 threads x 4/16/64 blocks per SM) on the real operands
- * and keeps the fastest; results do not depend on the shape.  Returns the number
- * of tuned (kind, elements) entries of h and copies up to cap of them (any
- * pointer may be NULL).
+ * and keeps the fastest; results do not depend on the shape.  On the
+ * tensor-core path (kind 2) the tensor-core kernel keeps one shape (one
+ * persistent 544-thread CTA per SM, bounded by its shared and tensor memory);
+ * the coupling kernel that follows it is tuned over six shapes (4, 8 or 16 rows
+ * per thread x 1, 2 or 4 groups of 128 threads) by timing whole first RK4 stages,
+ * before the response scan's graph capture or on the first uncaptured
+ * propagation of a size; a batched call keeps its entry in its first
+ * hierarchy.  For kind 2, block is threads per block and grid the coupling
+ * kernel's blocks per launch.  elements = state elements of the launch (all
+ * branches, ADOs and sets).  Returns the number of tuned (kind, elements)
+ * entries of h and copies up to cap of them (any pointer may be NULL).
  */
 int heom_get_tuning(const heom_hier *h, int cap, int *kind, int64_t *elements, int *block, int *grid);
 
@@ -399,6 +407,16 @@ heom_status heom_set_wait_limit_ns(heom_hier *h, uint64_t ns);
  * switches the injection off (the default).  Process-wide.
  */
 void heom_debug_fail_alloc(int64_t after);
+
+/*
+ * Shape override of the tensor-core path's coupling kernel for tests (no
+ * counterpart in the paper): shape 0-5 (8x2, 4x2, 4x4, 8x1, 16x1, 8x4 rows per
+ * thread x groups of 128 threads) replaces the autotuner's choice in every
+ * following launch; -1 restores tuning.  Results do not depend on the shape:
+ * every shape performs the same rounded operations per element.  Process-wide;
+ * HEOM_EINVAL outside -1..5.
+ */
+heom_status heom_debug_force_tc_shape(int shape);
 
 void heom_free_hier(heom_hier *h);
 void heom_free_state(heom_state *s);

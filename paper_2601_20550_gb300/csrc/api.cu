@@ -321,6 +321,9 @@ void response_2d_rows_impl(heom_hier *h, const heom_state *eq, const heom_grid *
       rk4_steps<R>(h, BR, Y, WA, B, dt, n2[it] - t_now, st, M.precision);
       t_now = n2[it];
       kick_into<R>(h, BR, Y, B, 1, st);
+      // the coupling kernel's shape is tuned (once per size) before the capture
+      if (sizeof(R) == 4 && M.precision == HEOM_TC)
+        tc_tune({TcRk4Set{&h->tc, (float2 *)Y, (float2 *)WA, (float2 *)WB, B}}, dt, st);
       // the t3 scan (n3 samples of m RK4 steps and two traces) is captured once
       // into a CUDA graph and replayed as a single launch
       GraphCapture cap(st);
@@ -903,6 +906,8 @@ heom_status heom_set_wait_limit_ns(heom_hier *h, uint64_t ns) {
 
 void heom_debug_fail_alloc(int64_t after) { g_alloc_budget.store(after < 0 ? -1 : after); }
 
+heom_status heom_debug_force_tc_shape(int shape) { return tc_force_shape(shape) ? HEOM_OK : HEOM_EINVAL; }
+
 void heom_free_hier(heom_hier *h) { delete h; }
 void heom_free_state(heom_state *s) { delete s; }
 
@@ -924,6 +929,15 @@ extern "C" int heom_get_tuning(const heom_hier *h, int cap, int *kind, int64_t *
       if (elements) elements[k] = e.first.second;
       if (block) block[k] = e.second.first;
       if (grid) grid[k] = e.second.second;
+    }
+    ++k;
+  }
+  for (const auto &e : h->tc.vt_tuned) {
+    if (k < cap) {
+      if (kind) kind[k] = 2;
+      if (elements) elements[k] = e.first;
+      if (block) block[k] = e.second.block;
+      if (grid) grid[k] = (int)e.second.grid;
     }
     ++k;
   }

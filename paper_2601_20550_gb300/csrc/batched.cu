@@ -251,6 +251,7 @@ static void response_2d_multi_tc(heom_hier *const *hs, const heom_state *const *
       t_now = n2[it];
       for (int k = 0; k < n_sets; ++k)
         kick_into<float>(hs[k], (const float2 *)S[k].P[0]->p, (float2 *)S[k].P[1]->p, B, 1, st);
+      tc_tune(scan, dt, st);   // coupling-kernel shape, once per size, before the capture
       GraphCapture cap(st);
       for (int kk = 0; kk < n3; ++kk) {
         if (kk > 0) tc_rk4_sets(scan, dt, m, st);

@@ -27,6 +27,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <atomic>
 #include <cstring>
 #include <stdexcept>
 
@@ -513,18 +514,19 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(const __grid_cons
 //             + alpha * (-gamma_n w_n[a][b] + sum_q kappa_q(a, b) w_{nb_q}[a][b]),
 //   kappa_q = -i cA_q (lam_s[a_s] - lam_s[b_s]) + cB_q (lam_s[a_s] + lam_s[b_s]),
 // over the coupling list of the ADO (up- and down-neighbours of every mode).
-// One block per (item, 16-row band); thread = (column b, row parity), 8 rows
-// per thread held in registers.  The coupling list is the outer loop, so each
-// neighbour's constants are read once per block and every thread has 8
-// independent loads in flight per neighbour.  No shared-memory tiles: the kernel
-// runs at high occupancy.  The block raises the item's running maximum |out|,
-// which the tensor-core kernel cleared, with one atomic per warp.
-constexpr int kVtThreads = 256;
-constexpr int kVtRowsPerThread = 8;
-constexpr int kVtRows = 2 * kVtRowsPerThread;
+// One block per (item, band of kRows = kRpt x kGroups rows); thread = (column b,
+// row group), kRpt rows per thread held in registers (rows a0, a0 + kGroups, ...).
+// The coupling list is the outer loop, so each neighbour's constants are read
+// once per block and every thread has kRpt independent loads in flight per
+// neighbour.  No shared-memory tiles: the kernel runs at high occupancy.  The
+// block raises the item's running maximum |out|, which the tensor-core kernel
+// cleared, with one atomic per warp.  The shape (kRpt, kGroups) is chosen per
+// size by the autotuner (tc_tune); results do not depend on it.
 constexpr int kMaxNb = 32;
 
-__global__ void __launch_bounds__(kVtThreads) vterm_kernel(const __grid_constant__ TcArgs P) {
+template <int kRpt, int kGroups>
+__global__ void __launch_bounds__(128 * kGroups) vterm_kernel(const __grid_constant__ TcArgs P) {
+  constexpr int kRows = kRpt * kGroups;
   int ks = 0;   // the parameter set of this block (blocks are concatenated set after set)
   while (ks + 1 < P.n_sets && (int64_t)blockIdx.x >= P.sets[ks + 1].vt_begin) ++ks;
   const TcSet &S = P.sets[ks];
@@ -538,23 +540,23 @@ __global__ void __launch_bounds__(kVtThreads) vterm_kernel(const __grid_constant
   const float2 *wb = S.w + br * S.n_ado * dd;
   const float alpha = P.alpha;
   const int b = threadIdx.x & 127, par = threadIdx.x >> 7;
-  const int a0 = band * kVtRows + par;          // rows a0, a0 + 2, ..., a0 + 14
+  const int a0 = band * kRows + par;            // rows a0, a0 + kGroups, ...
   // lanes past the last column keep running (no loads or stores) so that the
   // warp-wide maximum below sees every lane
-  const int nrow = b < d ? max(0, min(kVtRowsPerThread, (d - a0 + 1) / 2)) : 0;
-  const int64_t e0 = (int64_t)a0 * d + b, es = 2 * (int64_t)d;
-  float re[kVtRowsPerThread], im[kVtRowsPerThread];
+  const int nrow = b < d ? max(0, min(kRpt, (d - a0 + kGroups - 1) / kGroups)) : 0;
+  const int64_t e0 = (int64_t)a0 * d + b, es = (int64_t)kGroups * d;
+  float re[kRpt], im[kRpt];
 #pragma unroll
-  for (int j = 0; j < kVtRowsPerThread; ++j) re[j] = im[j] = 0.f;
+  for (int j = 0; j < kRpt; ++j) re[j] = im[j] = 0.f;
   const int *off = S.nb_off + n * nm;
   for (int s = 0; s < nm; ++s) {
     const int lo = off[s], hi = off[s + 1];
     if (lo == hi) continue;
     const float lb = S.lam[s * 128 + b];
-    float f[kVtRowsPerThread], g[kVtRowsPerThread];
+    float f[kRpt], g[kRpt];
 #pragma unroll
-    for (int j = 0; j < kVtRowsPerThread; ++j) {
-      const int a = min(a0 + 2 * j, d - 1);
+    for (int j = 0; j < kRpt; ++j) {
+      const int a = min(a0 + kGroups * j, d - 1);
       const float la = S.lam[s * 128 + a];
       f[j] = la - lb;
       g[j] = la + lb;
@@ -562,43 +564,45 @@ __global__ void __launch_bounds__(kVtThreads) vterm_kernel(const __grid_constant
     for (int q = lo; q < hi; ++q) {
       const float2 *wm = wb + (int64_t)S.nb_idx[q] * dd + e0;
       const float cA = S.nb_cA[q], cB = S.nb_cB[q];
-      float2 x[kVtRowsPerThread];
+      float2 x[kRpt];
 #pragma unroll
-      for (int j = 0; j < kVtRowsPerThread; ++j) x[j] = j < nrow ? wm[j * es] : make_float2(0.f, 0.f);
+      for (int j = 0; j < kRpt; ++j) x[j] = j < nrow ? wm[j * es] : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < kVtRowsPerThread; ++j) {
+      for (int j = 0; j < kRpt; ++j) {
+        // explicit fused operations: every shape rounds each element identically
         const float pc = cB * g[j], qc = cA * f[j];
-        re[j] += pc * x[j].x + qc * x[j].y;
-        im[j] += pc * x[j].y - qc * x[j].x;
+        re[j] = __fmaf_rn(qc, x[j].y, __fmaf_rn(pc, x[j].x, re[j]));
+        im[j] = __fmaf_rn(-qc, x[j].x, __fmaf_rn(pc, x[j].y, im[j]));
       }
     }
   }
   {  // decay: - gamma_n w_n
     const float dec = (float)S.decay[n];
     const float2 *wn = wb + (int64_t)n * dd + e0;
-    float2 x[kVtRowsPerThread];
+    float2 x[kRpt];
 #pragma unroll
-    for (int j = 0; j < kVtRowsPerThread; ++j) x[j] = j < nrow ? wn[j * es] : make_float2(0.f, 0.f);
+    for (int j = 0; j < kRpt; ++j) x[j] = j < nrow ? wn[j * es] : make_float2(0.f, 0.f);
 #pragma unroll
-    for (int j = 0; j < kVtRowsPerThread; ++j) {
-      re[j] -= dec * x[j].x;
-      im[j] -= dec * x[j].y;
+    for (int j = 0; j < kRpt; ++j) {
+      re[j] = __fmaf_rn(-dec, x[j].x, re[j]);
+      im[j] = __fmaf_rn(-dec, x[j].y, im[j]);
     }
   }
   const float2 *yb = S.y + item * dd + e0;
   const float2 *tb = S.tpart + item * dd + e0;
   float2 *ob = S.out + item * dd + e0;
-  float2 yv[kVtRowsPerThread], tv[kVtRowsPerThread];
+  float2 yv[kRpt], tv[kRpt];
 #pragma unroll
-  for (int j = 0; j < kVtRowsPerThread; ++j) {
+  for (int j = 0; j < kRpt; ++j) {
     yv[j] = j < nrow ? __ldcs(yb + j * es) : make_float2(0.f, 0.f);
     tv[j] = j < nrow ? __ldcs(tb + j * es) : make_float2(0.f, 0.f);
   }
   float omax = 0.f;
 #pragma unroll
-  for (int j = 0; j < kVtRowsPerThread; ++j)
+  for (int j = 0; j < kRpt; ++j)
     if (j < nrow) {
-      const float2 v = make_float2(yv[j].x + tv[j].x + alpha * re[j], yv[j].y + tv[j].y + alpha * im[j]);
+      const float2 v = make_float2(__fmaf_rn(alpha, re[j], __fadd_rn(yv[j].x, tv[j].x)),
+                                   __fmaf_rn(alpha, im[j], __fadd_rn(yv[j].y, tv[j].y)));
       omax = fmaxf(omax, fmaxf(fabsf(v.x), fabsf(v.y)));
       __stcs(ob + j * es, v);
     }
@@ -710,10 +714,32 @@ void tc_build(TcOperators &tc, const Model &M, const VbModel &vb, std::vector<vo
 
 bool tc_supported(const TcOperators &tc) { return tc.ready; }
 
+// Shapes of the coupling kernel the autotuner chooses from: rows per thread x
+// row groups (128 threads each) per block.
+struct VtShape {
+  int rpt, groups;
+};
+constexpr VtShape kVtShapes[] = {{8, 2}, {4, 2}, {4, 4}, {8, 1}, {16, 1}, {8, 4}};
+constexpr int kVtShapeCount = (int)(sizeof(kVtShapes) / sizeof(kVtShapes[0]));
+
+static void launch_vterm(int shape, int64_t blocks, const TcArgs &a, cudaStream_t st) {
+  const unsigned g = (unsigned)blocks;
+  switch (shape) {
+    case 1: vterm_kernel<4, 2><<<g, 256, 0, st>>>(a); break;
+    case 2: vterm_kernel<4, 4><<<g, 512, 0, st>>>(a); break;
+    case 3: vterm_kernel<8, 1><<<g, 128, 0, st>>>(a); break;
+    case 4: vterm_kernel<16, 1><<<g, 128, 0, st>>>(a); break;
+    case 5: vterm_kernel<8, 4><<<g, 512, 0, st>>>(a); break;
+    default: vterm_kernel<8, 2><<<g, 256, 0, st>>>(a); break;
+  }
+}
+
 // One RK4 stage, out = y + alpha L(w), of every set: one tensor-core launch and
-// one coupling-kernel launch for all of them.  which = 0..3 selects the Horner
-// stage's buffers (w, out, tpart, max_in, max_out) of each set.
-static void tc_stage_sets(const std::vector<TcRk4Set> &sets, int which, float alpha, cudaStream_t st) {
+// one coupling-kernel launch (of the given shape) for all of them.  which = 0..3
+// selects the Horner stage's buffers (w, out, tpart, max_in, max_out) of each
+// set.  Returns the coupling kernel's block count.
+static int64_t tc_stage_sets(const std::vector<TcRk4Set> &sets, int which, float alpha, int shape, cudaStream_t st) {
+  const int rows = kVtShapes[shape].rpt * kVtShapes[shape].groups;
   TcArgs a;
   std::memset(&a, 0, sizeof a);
   a.n_sets = (int)sets.size();
@@ -752,7 +778,7 @@ static void tc_stage_sets(const std::vector<TcRk4Set> &sets, int which, float al
     S.d = tc.d;
     S.n_ado = tc.n_ado;
     S.n_modes = tc.n_modes;
-    S.bands = (tc.d + kVtRows - 1) / kVtRows;   // 16-row bands
+    S.bands = (tc.d + rows - 1) / rows;
     S.item_begin = items;
     S.vt_begin = blocks;
     const int64_t n = (int64_t)R.branches * tc.n_ado;
@@ -760,15 +786,72 @@ static void tc_stage_sets(const std::vector<TcRk4Set> &sets, int which, float al
     blocks += n * S.bands;
   }
   a.n_items = items;
-  if (items == 0) return;
+  if (items == 0) return 0;
   if (blocks > 0x7fffffffLL) throw std::invalid_argument("too many work items for one stage launch");
   const int grid = (int)std::min<int64_t>(items, sets[0].tc->sms);
   if (a.n_sets > 1)
     tc_stage_kernel<true><<<grid, kThreads, kSmemDyn, st>>>(a);
   else
     tc_stage_kernel<false><<<grid, kThreads, kSmemDyn, st>>>(a);
-  vterm_kernel<<<(unsigned)blocks, kVtThreads, 0, st>>>(a);
+  launch_vterm(shape, blocks, a, st);
   count_launch(2);
+  return blocks;
+}
+
+static int64_t total_elements(const std::vector<TcRk4Set> &sets) {
+  int64_t e = 0;
+  for (const TcRk4Set &R : sets) e += (int64_t)R.branches * R.tc->n_ado * R.tc->d * R.tc->d;
+  return e;
+}
+
+// Coupling-kernel shape for a launch over these sets: the tuned one for their
+// total size (kept by the first set's hierarchy), else the default.  Outside a
+// stream capture, an untuned size is tuned first: every candidate shape times
+// three first-stage launches after one untimed one.  The first stage reads only
+// y and its item maxima and writes scratch (wa and its maxima) that the RK4
+// step overwrites, so tuning changes no result.  Needs the item maxima of y.
+static std::atomic<int> g_forced_shape{-1};
+
+bool tc_force_shape(int shape) {
+  if (shape < -1 || shape >= kVtShapeCount) return false;
+  g_forced_shape.store(shape);
+  return true;
+}
+
+static int vterm_shape(const std::vector<TcRk4Set> &sets, double dt, cudaStream_t st) {
+  const int forced = g_forced_shape.load();
+  if (forced >= 0) return forced;
+  TcOperators &t0 = *sets[0].tc;
+  const int64_t key = total_elements(sets);
+  auto it = t0.vt_tuned.find(key);
+  if (it != t0.vt_tuned.end()) return it->second.shape;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    (void)cudaGetLastError();
+    return 0;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    (void)cudaGetLastError();
+    return 0;
+  }
+  TcTuned best{0, 0, 0, 1e30f};
+  bool ok = true;
+  for (int c = 0; c < kVtShapeCount && ok; ++c) {
+    const int64_t blocks = tc_stage_sets(sets, 0, (float)(dt / 4), c, st);
+    cudaEventRecord(e0, st);
+    for (int r = 0; r < 3; ++r) tc_stage_sets(sets, 0, (float)(dt / 4), c, st);
+    cudaEventRecord(e1, st);
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) ok = false;
+    if (ok && ms < best.ms) best = TcTuned{c, 128 * kVtShapes[c].groups, blocks, ms};
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!ok) return 0;
+  t0.vt_tuned[key] = best;
+  return best.shape;
 }
 
 void tc_reserve(TcOperators &tc, int64_t n_items) {
@@ -780,8 +863,9 @@ void tc_reserve(TcOperators &tc, int64_t n_items) {
   tc.max_items = n_items;
 }
 
-void tc_rk4_sets(const std::vector<TcRk4Set> &sets, double dt, int64_t nsteps, cudaStream_t st) {
-  if (sets.empty() || nsteps <= 0) return;
+// Item maxima of every set's y (the first stage's input scaling); false if the
+// sets hold no work item.
+static bool tc_prologue(const std::vector<TcRk4Set> &sets, cudaStream_t st) {
   if ((int)sets.size() > kTcMaxSets) throw std::invalid_argument("too many parameter sets for one stage launch");
   bool any = false;
   for (const TcRk4Set &R : sets) {
@@ -792,12 +876,23 @@ void tc_rk4_sets(const std::vector<TcRk4Set> &sets, double dt, int64_t nsteps, c
     item_max_kernel<<<(unsigned)n_items, 256, 0, st>>>(R.y, (int64_t)R.tc->d * R.tc->d, R.tc->maxbuf);
     count_launch(1);
   }
-  if (!any) return;
+  return any;
+}
+
+void tc_tune(const std::vector<TcRk4Set> &sets, double dt, cudaStream_t st) {
+  if (sets.empty() || !tc_prologue(sets, st)) return;
+  vterm_shape(sets, dt, st);
+}
+
+void tc_rk4_sets(const std::vector<TcRk4Set> &sets, double dt, int64_t nsteps, cudaStream_t st) {
+  if (sets.empty() || nsteps <= 0) return;
+  if (!tc_prologue(sets, st)) return;
+  const int shape = vterm_shape(sets, dt, st);
   for (int64_t s = 0; s < nsteps; ++s) {
-    tc_stage_sets(sets, 0, (float)(dt / 4), st);
-    tc_stage_sets(sets, 1, (float)(dt / 3), st);
-    tc_stage_sets(sets, 2, (float)(dt / 2), st);
-    tc_stage_sets(sets, 3, (float)dt, st);
+    tc_stage_sets(sets, 0, (float)(dt / 4), shape, st);
+    tc_stage_sets(sets, 1, (float)(dt / 3), shape, st);
+    tc_stage_sets(sets, 2, (float)(dt / 2), shape, st);
+    tc_stage_sets(sets, 3, (float)dt, shape, st);
   }
 }
 

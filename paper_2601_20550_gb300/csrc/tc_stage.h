@@ -7,6 +7,7 @@
 #pragma once
 
 #include <cstdint>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -25,6 +26,16 @@ struct DeviceOom : std::bad_alloc {
   const char *what() const noexcept override { return "device allocation failed"; }
 };
 
+// Coupling-kernel shape chosen by the autotuner for one launch size: index into
+// the kernel's candidate list, threads per block, blocks per launch, and the
+// time of three first-stage launches (tensor-core and coupling kernel) in ms.
+struct TcTuned {
+  int shape;
+  int block;
+  int64_t grid;
+  float ms;
+};
+
 struct TcOperators {
   bool ready = false;
   int d = 0, n_ado = 0, n_modes = 0, n_hpieces = 3;
@@ -39,6 +50,7 @@ struct TcOperators {
   int sms = 0;
   unsigned *maxbuf = nullptr;     // workspace: per-item max |w| of y, wa, wb (grown on demand)
   int64_t max_items = 0;
+  std::map<int64_t, TcTuned> vt_tuned;  // by total state elements of the launch
 };
 
 // Prepare the tensor-core operator images of M (device allocations are appended
@@ -67,5 +79,14 @@ struct TcRk4Set {
 // alpha (-gamma w + sum kappa w_nb) (the coupling kernel).  Per item the
 // arithmetic does not depend on the other sets, so results equal per-set calls.
 void tc_rk4_sets(const std::vector<TcRk4Set> &sets, double dt, int64_t nsteps, cudaStream_t st);
+
+// Tune the coupling kernel's shape for a launch over these sets (outside any
+// stream capture; a size tuned before is not re-timed).  The sets' y must hold
+// the state the launches will see; wa receives scratch.  tc_rk4_sets tunes an
+// untuned size itself when it is not being captured.
+void tc_tune(const std::vector<TcRk4Set> &sets, double dt, cudaStream_t st);
+// Use coupling-kernel shape `shape` (0-5) for every launch instead of the tuned
+// one, or tune again (-1).  Process-wide; false if shape is out of range.
+bool tc_force_shape(int shape);
 
 }  // namespace heom

@@ -103,6 +103,7 @@ def lib():
         "heom_ckpt_verify": [ct.c_char_p, ct.POINTER(ct.c_uint64)],
         "heom_state_save": [_P, ct.c_char_p],
         "heom_state_load": [_P, ct.c_char_p],
+        "heom_debug_force_tc_shape": [ct.c_int],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -460,6 +461,11 @@ def heom_set_wait_limit_ns(h, ns):
 def heom_debug_fail_alloc(after):
     """Make device allocations fail after `after` more successes (after < 0: off)."""
     lib().heom_debug_fail_alloc(int(after))
+
+
+def heom_debug_force_tc_shape(shape):
+    """Force the tensor-core path's coupling-kernel shape (0-5), or -1 to tune again."""
+    _check(lib().heom_debug_force_tc_shape(int(shape)))
 
 
 def heom_launch_count():

@@ -321,6 +321,41 @@ def test_autotuner_picks_a_shape_once():
 
 
 @pytest.mark.gpu
+def test_tensor_core_coupling_shapes_and_tuning():
+    """Every coupling-kernel shape of the tensor-core path gives the same response bit
+    for bit (and the oracle's within the mixed-path tolerance); the autotuner records
+    one shape per launch size (kind 2) and keeps it."""
+    model = W.small_three_mode(n=3, depth_L=2)
+    grid = W.grid(0.5, 4, 6, 5, (0.0,), t_eq_fs=20.0)
+    h = H.heom_build_hierarchy(model, H.TC)
+    eq = H.heom_equilibrate(h, grid["dt_fs"], grid["t_eq_fs"], 0.0)
+    got = []
+    try:
+        for shape in range(6):
+            H.heom_debug_force_tc_shape(shape)
+            got.append(H.heom_response_2d(h, eq, grid))
+    finally:
+        H.heom_debug_force_tc_shape(-1)
+    for ri, rii, sc in got[1:]:
+        assert np.array_equal(ri, got[0][0]) and np.array_equal(rii, got[0][1]) and np.array_equal(sc, got[0][2])
+    assert [e for e in H.heom_get_tuning(h) if e[0] == 2] == []   # forced shapes are not recorded
+    RI, RII, SC = H.heom_response_2d(h, eq, grid)
+    assert np.array_equal(RI, got[0][0]) and np.array_equal(SC, got[0][2])
+    tuned = [e for e in H.heom_get_tuning(h) if e[0] == 2]
+    B = 2 * grid["n1"]
+    assert len(tuned) == 1 and tuned[0][1] == B * h.n_ado * h.d * h.d
+    assert tuned[0][2] in (128, 256, 512)
+    assert any(tuned[0][3] == B * h.n_ado * -(-h.d // r) and tuned[0][2] == t for r, t in
+               ((16, 256), (8, 256), (16, 512), (8, 128), (16, 128), (32, 512)))
+    H.heom_response_2d(h, eq, grid)
+    assert [e for e in H.heom_get_tuning(h) if e[0] == 2] == tuned
+    _, RIo, RIIo, SCo = OH.spectrum_2d(OM.Problem(model), grid)
+    scale = max(np.abs(RIo).max(), np.abs(RIIo).max())
+    assert np.abs(RI - RIo).max() < 1e-4 * scale
+    assert np.abs(SC - SCo).max() < 1e-4 * np.abs(SCo).max()
+
+
+@pytest.mark.gpu
 def test_batched_one_launch_equals_per_set():
     """Three FP64 sets of different basis size advanced together match per-set calls."""
     grid = W.grid(0.5, 3, 5, 4, (0.0, 2.0), t_eq_fs=12.0)
