@@ -1,0 +1,82 @@
+"""Pins for the 2D correlation spectrum's sign convention and the paper's water tables.
+
+  * Two-level closed form: a mode reduced to its two lowest harmonic levels, with no
+    bath, carries exactly the 0 -> 1 -> 0 pathways.  From Eqs. RFTIRI, echo and
+    virtual-echo, R_I = -2 i mu01^4 exp(i w (t1 - t3)) and R_II = -2 i mu01^4
+    exp(-i w (t1 + t3)), independent of t2 (the population difference is stationary).
+    With w on the Fourier grid, w = 2 pi p0 / (N dtau), the trapezoid sums of Eqs.
+    2D-rephasing and 2D-nonrephasing and the flip of Eq. correlation-spectrum give
+        S_C(q, p) = -4 mu01^4 dtau^2 a(q - p0) a(p - p0),
+        a(0) = N - 1/2,  a(x != 0 mod N) = -1/2,
+    so the printed equations make the 0 -> 1 -> 0 diagonal peak negative.
+  * Table readings (workloads.paper_water_model): the isolated cubic stretch of
+    Table (i) has its fundamental at the paper's diagonal stretch peak (about
+    3400 cm^-1) and the bend near its 1710 cm^-1; the printed direction of the
+    g_{s^3} normalisation would put the bend's lowest levels outside the cubic well.
+"""
+import math
+
+import numpy as np
+
+import workloads as W
+from oracle import heom as Hm
+from oracle import model as M
+
+C_CM_PER_FS = 2.99792458e-5
+
+
+def two_level_model(omega_cm, mu1):
+    md = W.mode("cubic", omega_cm, g3_cm=0.0, n_levels=2, n_prim=2, mu1=mu1, K_pade=1)
+    md["zeta_cm"] = 0.0
+    return {"modes": [md], "pairs": [], "T_K": 300.0, "depth_L": 1}
+
+
+def test_two_level_correlation_spectrum_closed_form():
+    N, dtau, p0 = 16, 4.0, 3
+    omega_cm = p0 / (N * dtau * C_CM_PER_FS)        # w = 2 pi p0 / (N dtau)
+    mu1 = 1.3
+    model = two_level_model(omega_cm, mu1)
+    prob = M.Problem(model)
+    grid = W.grid(0.125, 32, N, N, (0.0, 8.0), t_eq_fs=4.0)
+    rho_eq, RI, RII, SC = Hm.spectrum_2d(prob, grid)
+    mu01 = mu1 / math.sqrt(2.0)                    # <0|q|1> of the harmonic basis
+    t = np.arange(N) * dtau
+    w = omega_cm * 2.0 * math.pi * C_CM_PER_FS
+    t1, t3 = np.meshgrid(t, t, indexing="ij")
+    cI = -2j * mu01 ** 4 * np.exp(1j * w * (t1 - t3))
+    cII = -2j * mu01 ** 4 * np.exp(-1j * w * (t1 + t3))
+    for it in range(2):
+        # RK4 phase error over up to 2 x 15 x 32 steps of w dt = 0.037
+        assert np.abs(RI[it] - cI).max() < 1e-6 * np.abs(cI).max()
+        assert np.abs(RII[it] - cII).max() < 1e-6 * np.abs(cII).max()
+    a = np.full(N, -0.5)
+    a[0] = N - 0.5
+    q = np.arange(N)
+    ref = -4.0 * mu01 ** 4 * dtau ** 2 * np.outer(a[(q - p0) % N], a[(q - p0) % N])
+    for it in range(2):
+        assert np.abs(SC[it] - ref).max() < 1e-5 * np.abs(ref).max()
+    assert SC[0, p0, p0] < 0 and SC[0, p0, p0] == SC[0].min()
+
+
+def test_paper_table_readings():
+    model = W.paper_water_model(2)
+    stretch, bend = model["modes"]
+    E, _ = M.mode_basis(stretch)
+    w01 = (E[1] - E[0]) / M.CM_TO_RADFS
+    assert abs(w01 - 3400.0) < 10.0
+    E, _ = M.mode_basis(bend)
+    assert abs((E[1] - E[0]) / M.CM_TO_RADFS - 1710.0) < 10.0
+    # the anharmonic shifts are negative and of a vibrational size (tens to hundreds of cm^-1)
+    for md in (stretch, bend):
+        E, _ = M.mode_basis(md)
+        shift = ((E[2] - E[1]) - (E[1] - E[0])) / M.CM_TO_RADFS
+        assert -400.0 < shift < -1.0
+    # the printed direction of the cubic normalisation, g = g~ (omega_0/nu)^3 omega_0
+    inv = dict(bend)
+    inv["g3_cm"] = -0.7 * (4000.0 / 1710.0) ** 3 * 4000.0
+    E, _ = M.mode_basis(inv)
+    assert (E[1] - E[0]) / M.CM_TO_RADFS > 1.0e4
+    # the three-mode tables build (d = 64) with every pair of FitAll2
+    m3 = W.paper_water_model(3)
+    assert len(m3["modes"]) == 3 and len(m3["pairs"]) == 3
+    assert M.Problem(W.paper_water_model(3, depth_L=1)).d == 64

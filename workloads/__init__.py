@@ -161,6 +161,74 @@ def c5_batch(n_sets=16, seed=2605):
     return out
 
 
+# ---------------------------------------------------------------------------
+# The paper's own water parameter sets (Sec. IV, Tables (i), (ii) and FitAll2)
+# ---------------------------------------------------------------------------
+# The tables give dimensionless ("tilde") values against the unit frequency
+# omega_0 = 4000 cm^-1.  Readings (the printed normalisations are partly garbled):
+#   * omega_s = nu_s (the table's frequency column); gamma_s = (gamma_s/omega_0) omega_0.
+#   * zeta_s = zeta~_s (nu_s/omega_0)^2 omega_0 (the printed definition solved for zeta_s).
+#   * V_LL = V~_LL omega_0/nu_s (zero in every table), V_SL = V~_SL.
+#   * Every power of q_s in a potential or dipole term carries one factor nu_s/omega_0:
+#     g_{s^3} = g~ (nu_s/omega_0)^3 omega_0, g_{ss'} = g~ (nu_s nu_s'/omega_0^2) omega_0,
+#     g_{s^2 s'} = g~ (nu_s/omega_0)^2 (nu_s'/omega_0) omega_0, g_{s s'^2} likewise,
+#     mu_s = mu~_s nu_s/omega_0, mu_ss = mu~_ss (nu_s/omega_0)^2, mu_ss' = mu~_ss' nu_s nu_s'/omega_0^2
+#     (mu in units of the paper's undefined mu_0; spectra are compared after normalisation).
+#     The mu_ss relation is the printed one; the printed g_{s^3} relation is the inverse,
+#     which puts the lowest four levels of the unbounded cubic wells far outside the
+#     harmonic range (bend fundamental above 1e5 cm^-1), whereas this reading puts the
+#     stretch fundamental at 3398 cm^-1, where the paper places its diagonal peak.
+#   * The two-mode caption's pair entries, written with the index 1', belong to the
+#     stretch-bend pair (1, 2); FitAll2's "-2,6 x 10^-2" is -2.6e-2.
+#   * T = 300 K (not printed); cubic modes in a harmonic basis of 16 states (the four
+#     kept levels converge to 1 cm^-1 there, and no state of the unbounded side of the
+#     cubic enters; a much larger primitive basis finds such states first).
+PAPER_OMEGA0_CM = 4000.0
+# Table (i), two-mode model, rows (1) stretch and (2) bend:
+#   nu_s (cm^-1), gamma_s/omega_0, zeta~, V~_LL, V~_SL, g~_{s^3}, mu~_s, mu~_ss
+PAPER_TABLE_I = ((3520.0, 5.0e-3, 9.0, 0.0, 1.0, -5.0e-1, 3.3, 1.2e-2),
+                 (1710.0, 2e-2, 0.8, 0.0, 1.0, -7e-1, 1.8, 0.0))
+# its caption's pair entries: g~_ss' (not given: 0), g~_{s^2 s'}, g~_{s s'^2}, mu~_ss'
+PAPER_TABLE_I_PAIRS = {(0, 1): (0.0, 0.0, 0.2, 2.0e-3)}
+# Table (ii), three-mode model, rows (1) asymmetric stretch, (1') symmetric stretch, (2) bend
+PAPER_TABLE_II = ((3570.0, 5.0e-3, 9.0, 0.0, 1.0, -5.0e-1, 3.3, 1.2e-2),
+                  (3470.0, 5.0e-3, 9.0, 0.0, 1.0, -5.0e-1, 3.3, 1.2e-2),
+                  (1710.0, 2e-2, 0.8, 0.0, 1.0, -7e-1, 1.8, 0.0))
+# Table FitAll2, pairs 1-1', 1-2, 1'-2: g~_ss', g~_{s^2 s'}, g~_{s s'^2}, mu~_ss'
+PAPER_FITALL2 = {(0, 1): (-5e-3, 0.32, -4.2e-3, 0.0),
+                 (0, 2): (1e-7, -2.6e-2, 4e-4, 2.0e-3),
+                 (1, 2): (-8e-4, 1.2e-1, -1.2e-2, 2.0e-3)}
+
+
+def paper_water_model(n_modes=2, n_levels=4, depth_L=3, K_pade=1, n_prim=16, T_K=300.0):
+    """The paper's two-mode (Table (i)) or three-mode (Tables (ii) and FitAll2)
+    water model with cubic potentials, read as stated above."""
+    rows, prs = ((PAPER_TABLE_I, PAPER_TABLE_I_PAIRS) if n_modes == 2 else
+                 (PAPER_TABLE_II, PAPER_FITALL2))
+    w0 = PAPER_OMEGA0_CM
+    modes = []
+    for nu, gam, zt, vll, vsl, g3, mu, muss in rows:
+        r = nu / w0
+        md = mode("cubic", nu, g3_cm=g3 * r ** 3 * w0, n_levels=n_levels, n_prim=n_prim,
+                  gamma_cm=gam * w0, V_LL=vll / r, V_SL=vsl, mu1=mu * r, mu2=muss * r ** 2,
+                  K_pade=K_pade)
+        md["zeta_cm"] = float(zt * r ** 2 * w0)
+        modes.append(md)
+    pairs = []
+    for (s, t), (g, g21, g12, mst) in sorted(prs.items()):
+        rs, rt = rows[s][0] / w0, rows[t][0] / w0
+        pairs.append(pair(s, t, g * rs * rt * w0, g21 * rs ** 2 * rt * w0, g12 * rs * rt ** 2 * w0,
+                          mst * rs * rt))
+    return {"modes": modes, "pairs": pairs, "T_K": float(T_K), "depth_L": int(depth_L)}
+
+
+def paper_water_grid(n=128, t2_fs=(0.0, 50.0, 100.0)):
+    """2D grid for the paper's water demonstrations: dt = 0.25 fs (the paper's three-mode
+    step), samples every 4 fs (m = 16; Nyquist 4170 cm^-1, above the stretch band),
+    n x n samples, t2 = 0, 50 and 100 fs."""
+    return grid(0.25, 16, n, n, t2_fs, t_eq_fs=200.0)
+
+
 CONFIGS = {"c1": c1, "c2": c2, "c3": c3, "c4": c4, "c5": c5}
 
 
