@@ -96,8 +96,9 @@ def algorithmic_costs(model, d, nado, ado_table, nb_counts, prec):
 # Measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per work item
 # (one ADO of one branch) of one RK4 stage of the tensor-core path: one ncu capture
 # of a 4-branch c3 case, scaled per item (the per-branch working set is the same at
-# 256 branches).  None when the stage kernels have changed since that capture.
-TC_STAGE_TRAFFIC_BYTES_PER_ITEM = 752.4e3
+# 256 branches), keyed by the coupling kernel's shape (threads, rows per block); a
+# shape without a capture of the current kernels reports no traffic.
+TC_STAGE_TRAFFIC_BYTES_PER_ITEM = {(256, 8): 760.4e3}
 
 
 class ClockSampler:
@@ -351,6 +352,8 @@ def main():
     ap.add_argument("--grad-fd", type=int, default=0,
                     help="c4-grad: check this many gradient entries (<= 4) against finite differences")
     ap.add_argument("--c5-precision", type=int, default=0, choices=[0, 1], help="c5-window: 0 FP64, 1 FP32")
+    ap.add_argument("--tc-shape", type=int, default=-1,
+                    help="force the tensor-core path's coupling-kernel shape 0-5 (profiling runs only)")
     ap.add_argument("--branches", type=int, default=0,
                     help="override the batch (profiling runs only; default 2*n1)")
     args = ap.parse_args()
@@ -382,6 +385,8 @@ def main():
     model, grid = W.config(cfg)
     h = H.heom_build_hierarchy(model, prec)
     d, nado = h.d, h.n_ado
+    if args.tc_shape >= 0:
+        H.heom_debug_force_tc_shape(args.tc_shape)
     # the FP64 equilibration of Sec. II.C.1 (timed: its share enters spectra/hour)
     H.heom_state_create(h, 1, 0)
     torch.cuda.synchronize()
@@ -476,8 +481,6 @@ def main():
         achieved = bytes_upd * per_launch_units / stage_s / 1e9
         peak = peaks["hbm_gbs"]
         traffic = None
-        if prec == 2 and TC_STAGE_TRAFFIC_BYTES_PER_ITEM:
-            traffic = TC_STAGE_TRAFFIC_BYTES_PER_ITEM * B * nado
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "RK4 stage (tc_stage_kernel + vterm_kernel)" if prec == 2 else "stage_kernel_vb",
@@ -490,10 +493,16 @@ def main():
         if prec == 2:
             # the coupling kernel's launch shape the autotuner chose for this batch
             tuned = [e for e in H.heom_get_tuning(h) if e[0] == 2 and e[1] == B * nado * d * d]
-            if tuned:
+            if args.tc_shape >= 0:
+                roof["coupling_kernel_shape"] = {"forced": args.tc_shape}
+            elif tuned:
                 bands = tuned[0][3] // (B * nado)
+                rows = -(-d // bands)
                 roof["coupling_kernel_shape"] = {"threads": tuned[0][2], "blocks": tuned[0][3],
-                                                 "rows_per_block": -(-d // bands)}
+                                                 "rows_per_block": rows}
+                per_item = TC_STAGE_TRAFFIC_BYTES_PER_ITEM.get((tuned[0][2], rows))
+                if per_item and cfg == "c3":
+                    roof["traffic"] = per_item * B * nado
 
     # ---------------- error against the FP64 path ----------------
     # (a) the timed traces: every branch of the timed batch started from the same
