@@ -96,9 +96,10 @@ def algorithmic_costs(model, d, nado, ado_table, nb_counts, prec):
 # Measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per work item
 # (one ADO of one branch) of one RK4 stage of the tensor-core path: one ncu capture
 # of a 4-branch c3 case, scaled per item (the per-branch working set is the same at
-# 256 branches), keyed by the coupling kernel's shape (threads, rows per block); a
-# shape without a capture of the current kernels reports no traffic.
-TC_STAGE_TRAFFIC_BYTES_PER_ITEM = {(256, 8): 760.4e3}
+# 256 branches), keyed by the coupling kernel's shape (rows per thread, row groups,
+# ADOs per block, flags); a shape without a capture of the current kernels reports
+# none.
+TC_STAGE_TRAFFIC_BYTES_PER_ITEM = {}
 
 
 class ClockSampler:
@@ -353,7 +354,7 @@ def main():
                     help="c4-grad: check this many gradient entries (<= 4) against finite differences")
     ap.add_argument("--c5-precision", type=int, default=0, choices=[0, 1], help="c5-window: 0 FP64, 1 FP32")
     ap.add_argument("--tc-shape", type=int, default=-1,
-                    help="force the tensor-core path's coupling-kernel shape 0-5 (profiling runs only)")
+                    help="force the tensor-core path's coupling-kernel shape 0-16 (profiling runs only)")
     ap.add_argument("--branches", type=int, default=0,
                     help="override the batch (profiling runs only; default 2*n1)")
     args = ap.parse_args()
@@ -496,11 +497,12 @@ def main():
             if args.tc_shape >= 0:
                 roof["coupling_kernel_shape"] = {"forced": args.tc_shape}
             elif tuned:
-                bands = tuned[0][3] // (B * nado)
-                rows = -(-d // bands)
-                roof["coupling_kernel_shape"] = {"threads": tuned[0][2], "blocks": tuned[0][3],
-                                                 "rows_per_block": rows}
-                per_item = TC_STAGE_TRAFFIC_BYTES_PER_ITEM.get((tuned[0][2], rows))
+                shape = H.heom_get_tc_shape(h, tuned[0][1])
+                roof["coupling_kernel_shape"] = {"rows_per_thread": shape[0], "row_groups": shape[1],
+                                                 "ados_per_block": shape[2], "l2_prefetch": shape[3] & 1,
+                                                 "two_sources_in_flight": shape[3] >> 1,
+                                                 "threads": tuned[0][2], "blocks": tuned[0][3]}
+                per_item = TC_STAGE_TRAFFIC_BYTES_PER_ITEM.get(tuple(shape))
                 if per_item and cfg == "c3":
                     roof["traffic"] = per_item * B * nado
 

@@ -221,8 +221,11 @@ heom_status heom_steady_state(heom_hier *h, double tol, int restart, int max_ite
  * and keeps the fastest; results do not depend on the shape.  On the
  * tensor-core path (kind 2) the tensor-core kernel keeps one shape (one
  * persistent 544-thread CTA per SM, bounded by its shared and tensor memory);
- * the coupling kernel that follows it is tuned over six shapes (4, 8 or 16 rows
- * per thread x 1, 2 or 4 groups of 128 threads) by timing whole first RK4 stages,
+ * the coupling kernel that follows it is tuned over seventeen shapes (2, 4, 8 or
+ * 16 rows per thread x 1 or 2 groups of 128 threads x 1, 2, 4 or 8 consecutive
+ * ADOs per block, with or without a bulk L2 prefetch of the block's sources and
+ * two neighbour sources in flight per thread; see
+ * heom_get_tc_shape) by timing whole first RK4 stages,
  * before the response scan's graph capture or on the first uncaptured
  * propagation of a size; a batched call keeps its entry in its first
  * hierarchy.  For kind 2, block is threads per block and grid the coupling
@@ -410,13 +413,28 @@ void heom_debug_fail_alloc(int64_t after);
 
 /*
  * Shape override of the tensor-core path's coupling kernel for tests (no
- * counterpart in the paper): shape 0-5 (8x2, 4x2, 4x4, 8x1, 16x1, 8x4 rows per
- * thread x groups of 128 threads) replaces the autotuner's choice in every
- * following launch; -1 restores tuning.  Results do not depend on the shape:
- * every shape performs the same rounded operations per element.  Process-wide;
- * HEOM_EINVAL outside -1..5.
+ * counterpart in the paper): shape 0-16 (rows per thread x groups of 128 threads x
+ * consecutive ADOs per block = 8x2x1, 4x2x1, 8x1x1, 4x2x2, 4x2x4, 4x1x4, 2x2x8,
+ * 4x1x8, then 8x1x1, 4x2x1, 8x2x1, 4x2x4, 16x1x1, 4x1x1 with a bulk L2 prefetch of
+ * each block's source bands, then 8x1x1, 4x1x1, 4x2x1 with the prefetch and two
+ * neighbour sources in flight per thread) replaces the autotuner's choice in
+ * every following launch; -1 restores tuning.  Results do not depend on the
+ * shape: every shape performs the same rounded operations per element, in
+ * ascending neighbour order.  Process-wide; HEOM_EINVAL outside -1..16.
  */
 heom_status heom_debug_force_tc_shape(int shape);
+
+/*
+ * The coupling-kernel shape the autotuner chose for tensor-core launches over
+ * `elements` state elements (the kind-2 entries of heom_get_tuning): rows per
+ * thread, row groups of 128 threads, consecutive ADOs per block (a block reads
+ * the union of those ADOs' neighbour states once) and flags: bit 0 set if the
+ * block first requests its source bands into L2, bit 1 set if each thread keeps
+ * two neighbour sources' loads in flight.  Returns 1 and fills the non-NULL
+ * outputs if such an entry exists, else 0.
+ */
+int heom_get_tc_shape(const heom_hier *h, int64_t elements, int *rows_per_thread, int *row_groups,
+                      int *ados_per_block, int *flags);
 
 void heom_free_hier(heom_hier *h);
 void heom_free_state(heom_state *s);

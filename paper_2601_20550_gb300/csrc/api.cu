@@ -908,6 +908,14 @@ void heom_debug_fail_alloc(int64_t after) { g_alloc_budget.store(after < 0 ? -1 
 
 heom_status heom_debug_force_tc_shape(int shape) { return tc_force_shape(shape) ? HEOM_OK : HEOM_EINVAL; }
 
+int heom_get_tc_shape(const heom_hier *h, int64_t elements, int *rows_per_thread, int *row_groups,
+                      int *ados_per_block, int *flags) {
+  if (!h) return 0;
+  auto it = h->tc.vt_tuned.find(elements);
+  if (it == h->tc.vt_tuned.end()) return 0;
+  return tc_shape_params(it->second.shape, rows_per_thread, row_groups, ados_per_block, flags) ? 1 : 0;
+}
+
 void heom_free_hier(heom_hier *h) { delete h; }
 void heom_free_state(heom_state *s) { delete s; }
 

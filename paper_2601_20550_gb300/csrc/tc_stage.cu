@@ -29,6 +29,7 @@
 #include <cmath>
 #include <atomic>
 #include <cstring>
+#include <map>
 #include <stdexcept>
 
 #include <cuda_fp16.h>
@@ -69,9 +70,12 @@ constexpr uint64_t kDrainNs = 2000000000ull;
 struct TcSet {
   const uint4 *himg;          // shared-memory images of the H' pieces
   const float *lam;           // [n_modes][128] lam_s[digit_s(a)]
-  const double *decay;        // [n_ado]
-  const int *nb_off, *nb_idx; // coupling lists
-  const float *nb_cA, *nb_cB;
+  // coupling kernel tables for groups of 1, 2, 4 and 8 consecutive ADOs: per group
+  // the union of its ADOs and their neighbours (offsets, ascending ADO indices) and
+  // per (member, ADO of the group) the term: (cA or the decay, cB, term, 0) with
+  // term = -2 none, -1 the decay, s >= 0 a coupling of mode s
+  const int *vt_uoff[4], *vt_uidx[4];
+  const float4 *vt_desc[4];
   const float2 *w, *y;        // stage input and step-start state
   float2 *out, *tpart;        // stage output; tensor-core part (may equal out, not w or y)
   const unsigned *max_in;     // per item: largest |component| of w (float bits)
@@ -514,102 +518,147 @@ __global__ void __launch_bounds__(kThreads, 1) tc_stage_kernel(const __grid_cons
 //             + alpha * (-gamma_n w_n[a][b] + sum_q kappa_q(a, b) w_{nb_q}[a][b]),
 //   kappa_q = -i cA_q (lam_s[a_s] - lam_s[b_s]) + cB_q (lam_s[a_s] + lam_s[b_s]),
 // over the coupling list of the ADO (up- and down-neighbours of every mode).
-// One block per (item, band of kRows = kRpt x kGroups rows); thread = (column b,
-// row group), kRpt rows per thread held in registers (rows a0, a0 + kGroups, ...).
-// The coupling list is the outer loop, so each neighbour's constants are read
-// once per block and every thread has kRpt independent loads in flight per
-// neighbour.  No shared-memory tiles: the kernel runs at high occupancy.  The
-// block raises the item's running maximum |out|, which the tensor-core kernel
-// cleared, with one atomic per warp.  The shape (kRpt, kGroups) is chosen per
-// size by the autotuner (tc_tune); results do not depend on it.
+// One block per (group of kAdos consecutive ADOs of one branch, band of
+// kRows = kRpt x kGroups rows); thread = (column b, row group), kRpt rows per
+// thread (rows a0, a0 + kGroups, ...) and kAdos accumulators per row held in
+// registers.  The block walks the union of the group's ADOs and their
+// neighbours in ascending ADO order (a host-built table of that union and, per
+// (member, ADO of the group), the term it contributes: none, the decay, or a
+// coupling of mode s with cA, cB), so each neighbour state is read once for the
+// whole group (lam through L1: no shared-memory staging or barrier before the
+// first gather).  Every element accumulates its own terms in ascending neighbour
+// index with explicit fused operations, so all shapes round identically.  The
+// block raises each item's running maximum |out|, which the tensor-core kernel
+// cleared, with one atomic per warp.  The shape is chosen per size by the
+// autotuner (tc_tune).
 constexpr int kMaxNb = 32;
 
-template <int kRpt, int kGroups>
+template <int kRpt, int kGroups, int kAdos, bool kPf, bool kTwo>
 __global__ void __launch_bounds__(128 * kGroups) vterm_kernel(const __grid_constant__ TcArgs P) {
   constexpr int kRows = kRpt * kGroups;
+  constexpr int kLog = kAdos == 1 ? 0 : kAdos == 2 ? 1 : kAdos == 4 ? 2 : 3;
   int ks = 0;   // the parameter set of this block (blocks are concatenated set after set)
   while (ks + 1 < P.n_sets && (int64_t)blockIdx.x >= P.sets[ks + 1].vt_begin) ++ks;
   const TcSet &S = P.sets[ks];
   const int d = S.d, nm = S.n_modes, bands = S.bands;
   const int64_t dd = (int64_t)d * d;
+  const int gpb = (S.n_ado + kAdos - 1) / kAdos;   // ADO groups per branch
   const int64_t lb = (int64_t)blockIdx.x - S.vt_begin;
-  const int64_t item = lb / bands;   // item within the set
-  const int band = (int)(lb - item * bands);
-  const int n = (int)(item % S.n_ado);
-  const int64_t br = item / S.n_ado;
+  const int64_t gi = lb / bands;                   // group within the set (branch-major)
+  const int band = (int)(lb - gi * bands);
+  const int64_t br = gi / gpb;
+  const int g = (int)(gi - br * gpb);
+  const int n0 = g * kAdos;
   const float2 *wb = S.w + br * S.n_ado * dd;
   const float alpha = P.alpha;
+  const float *__restrict__ lam = S.lam;   // [n_modes][128], read through L1
   const int b = threadIdx.x & 127, par = threadIdx.x >> 7;
-  const int a0 = band * kRows + par;            // rows a0, a0 + kGroups, ...
+  const int a0 = band * kRows + par;
   // lanes past the last column keep running (no loads or stores) so that the
-  // warp-wide maximum below sees every lane
+  // warp-wide maxima below see every lane
   const int nrow = b < d ? max(0, min(kRpt, (d - a0 + kGroups - 1) / kGroups)) : 0;
   const int64_t e0 = (int64_t)a0 * d + b, es = (int64_t)kGroups * d;
-  float re[kRpt], im[kRpt];
+  float re[kAdos][kRpt], im[kAdos][kRpt];
 #pragma unroll
-  for (int j = 0; j < kRpt; ++j) re[j] = im[j] = 0.f;
-  const int *off = S.nb_off + n * nm;
-  for (int s = 0; s < nm; ++s) {
-    const int lo = off[s], hi = off[s + 1];
-    if (lo == hi) continue;
-    const float lb = S.lam[s * 128 + b];
-    float f[kRpt], g[kRpt];
+  for (int k = 0; k < kAdos; ++k)
 #pragma unroll
-    for (int j = 0; j < kRpt; ++j) {
-      const int a = min(a0 + kGroups * j, d - 1);
-      const float la = S.lam[s * 128 + a];
-      f[j] = la - lb;
-      g[j] = la + lb;
-    }
-    for (int q = lo; q < hi; ++q) {
-      const float2 *wm = wb + (int64_t)S.nb_idx[q] * dd + e0;
-      const float cA = S.nb_cA[q], cB = S.nb_cB[q];
-      float2 x[kRpt];
+    for (int j = 0; j < kRpt; ++j) re[k][j] = im[k][j] = 0.f;
+  int arow[kRpt];
 #pragma unroll
-      for (int j = 0; j < kRpt; ++j) x[j] = j < nrow ? wm[j * es] : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < kRpt; ++j) {
-        // explicit fused operations: every shape rounds each element identically
-        const float pc = cB * g[j], qc = cA * f[j];
-        re[j] = __fmaf_rn(qc, x[j].y, __fmaf_rn(pc, x[j].x, re[j]));
-        im[j] = __fmaf_rn(-qc, x[j].x, __fmaf_rn(pc, x[j].y, im[j]));
+  for (int j = 0; j < kRpt; ++j) arow[j] = min(a0 + kGroups * j, d - 1);
+  const int *uoff = S.vt_uoff[kLog];
+  const int *uidx = S.vt_uidx[kLog];
+  const float4 *desc = S.vt_desc[kLog];
+  const int u0 = uoff[g], u1 = uoff[g + 1];
+  if (kPf && threadIdx.x < 32) {
+    // request the band of every source state (the union members, then y and tpart
+    // of each ADO of the group) into L2 up front, one bulk prefetch per lane, so
+    // that the gather rounds below find them there
+    const int r0 = band * kRows, nr = min(kRows, d - r0);
+    if (nr > 0) {
+      const int64_t off = (int64_t)r0 * d, bytes = (int64_t)nr * d * (int64_t)sizeof(float2);
+      const int nu = u1 - u0, nk = min(kAdos, S.n_ado - n0);
+      for (int i = threadIdx.x; i < nu + 2 * nk; i += 32) {
+        const float2 *src;
+        if (i < nu) {
+          src = wb + (int64_t)uidx[u0 + i] * dd + off;
+        } else {
+          const int64_t item = br * S.n_ado + n0 + ((i - nu) >> 1);
+          src = (((i - nu) & 1) ? S.tpart : S.y) + item * dd + off;
+        }
+        l2_prefetch_bulk(src, bytes);
       }
     }
   }
-  {  // decay: - gamma_n w_n
-    const float dec = (float)S.decay[n];
-    const float2 *wn = wb + (int64_t)n * dd + e0;
+  // the terms of union member u (states x of its rows) added to every ADO of the group
+  auto add_member = [&](int u, const float2 (&x)[kRpt]) {
+#pragma unroll
+    for (int k = 0; k < kAdos; ++k) {
+      const float4 t = desc[(int64_t)u * kAdos + k];   // (cA or decay, cB, term, -)
+      const int term = __float_as_int(t.z);
+      if (term == -1) {   // decay of the ADO itself: - gamma_n w_n
+#pragma unroll
+        for (int j = 0; j < kRpt; ++j) {
+          re[k][j] = __fmaf_rn(-t.x, x[j].x, re[k][j]);
+          im[k][j] = __fmaf_rn(-t.x, x[j].y, im[k][j]);
+        }
+      } else if (term >= 0) {   // coupling of mode `term`
+        const float lbv = __ldg(lam + term * 128 + b);
+#pragma unroll
+        for (int j = 0; j < kRpt; ++j) {
+          const float la = __ldg(lam + term * 128 + arow[j]);
+          const float pc = t.y * (la + lbv), qc = t.x * (la - lbv);
+          re[k][j] = __fmaf_rn(qc, x[j].y, __fmaf_rn(pc, x[j].x, re[k][j]));
+          im[k][j] = __fmaf_rn(-qc, x[j].x, __fmaf_rn(pc, x[j].y, im[k][j]));
+        }
+      }
+    }
+  };
+  int u = u0;
+  if (kTwo) {
+    // two members' loads in flight per thread (same per-element order: u, then u + 1)
+    for (; u + 1 < u1; u += 2) {
+      const float2 *wm0 = wb + (int64_t)uidx[u] * dd + e0;
+      const float2 *wm1 = wb + (int64_t)uidx[u + 1] * dd + e0;
+      float2 x0[kRpt], x1[kRpt];
+#pragma unroll
+      for (int j = 0; j < kRpt; ++j) {
+        x0[j] = j < nrow ? wm0[j * es] : make_float2(0.f, 0.f);
+        x1[j] = j < nrow ? wm1[j * es] : make_float2(0.f, 0.f);
+      }
+      add_member(u, x0);
+      add_member(u + 1, x1);
+    }
+  }
+  for (; u < u1; ++u) {
+    const float2 *wm = wb + (int64_t)uidx[u] * dd + e0;
     float2 x[kRpt];
 #pragma unroll
-    for (int j = 0; j < kRpt; ++j) x[j] = j < nrow ? wn[j * es] : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int j = 0; j < kRpt; ++j) {
-      re[j] = __fmaf_rn(-dec, x[j].x, re[j]);
-      im[j] = __fmaf_rn(-dec, x[j].y, im[j]);
-    }
+    for (int j = 0; j < kRpt; ++j) x[j] = j < nrow ? wm[j * es] : make_float2(0.f, 0.f);
+    add_member(u, x);
   }
-  const float2 *yb = S.y + item * dd + e0;
-  const float2 *tb = S.tpart + item * dd + e0;
-  float2 *ob = S.out + item * dd + e0;
-  float2 yv[kRpt], tv[kRpt];
 #pragma unroll
-  for (int j = 0; j < kRpt; ++j) {
-    yv[j] = j < nrow ? __ldcs(yb + j * es) : make_float2(0.f, 0.f);
-    tv[j] = j < nrow ? __ldcs(tb + j * es) : make_float2(0.f, 0.f);
+  for (int k = 0; k < kAdos; ++k) {
+    if (n0 + k >= S.n_ado) break;   // ragged last group (uniform across the block)
+    const int64_t item = br * S.n_ado + n0 + k;
+    const float2 *yb = S.y + item * dd + e0;
+    const float2 *tb = S.tpart + item * dd + e0;
+    float2 *ob = S.out + item * dd + e0;
+    float omax = 0.f;
+#pragma unroll
+    for (int j = 0; j < kRpt; ++j)
+      if (j < nrow) {
+        const float2 yv = __ldcs(yb + j * es), tv = __ldcs(tb + j * es);
+        const float2 v = make_float2(__fmaf_rn(alpha, re[k][j], __fadd_rn(yv.x, tv.x)),
+                                     __fmaf_rn(alpha, im[k][j], __fadd_rn(yv.y, tv.y)));
+        omax = fmaxf(omax, fmaxf(fabsf(v.x), fabsf(v.y)));
+        __stcs(ob + j * es, v);
+      }
+    // running max |out| of the item (the tensor-core kernel cleared it)
+#pragma unroll
+    for (int o2 = 16; o2 > 0; o2 >>= 1) omax = fmaxf(omax, __shfl_xor_sync(0xffffffffu, omax, o2));
+    if ((threadIdx.x & 31) == 0 && S.max_out) atomicMax(S.max_out + item, __float_as_uint(omax));
   }
-  float omax = 0.f;
-#pragma unroll
-  for (int j = 0; j < kRpt; ++j)
-    if (j < nrow) {
-      const float2 v = make_float2(__fmaf_rn(alpha, re[j], __fadd_rn(yv[j].x, tv[j].x)),
-                                   __fmaf_rn(alpha, im[j], __fadd_rn(yv[j].y, tv[j].y)));
-      omax = fmaxf(omax, fmaxf(fabsf(v.x), fabsf(v.y)));
-      __stcs(ob + j * es, v);
-    }
-  // running max |out| of the item (the tensor-core kernel cleared it)
-#pragma unroll
-  for (int o2 = 16; o2 > 0; o2 >>= 1) omax = fmaxf(omax, __shfl_xor_sync(0xffffffffu, omax, o2));
-  if ((threadIdx.x & 31) == 0 && S.max_out) atomicMax(S.max_out + item, __float_as_uint(omax));
 }
 
 // Largest component magnitude of every item of a state (bit pattern of a
@@ -630,6 +679,12 @@ __global__ void __launch_bounds__(256) item_max_kernel(const float2 *__restrict_
 }
 
 }  // namespace
+
+static float bits_as_float(int v) {
+  float f;
+  std::memcpy(&f, &v, 4);
+  return f;
+}
 
 static uint16_t half_bits(double x) {
   __half h = __double2half(x);
@@ -697,11 +752,50 @@ void tc_build(TcOperators &tc, const Model &M, const VbModel &vb, std::vector<vo
   for (int n = 0; n < M.n_ado; ++n)
     if (M.nb_off[(size_t)n * M.n_modes + M.n_modes] - M.nb_off[(size_t)n * M.n_modes] > kMaxNb)
       throw std::invalid_argument("tensor-core path supports at most 32 coupling entries per ADO");
-  tc.decay = vb.decay;
-  tc.nb_off = vb.nb_off;
-  tc.nb_idx = vb.nb_idx;
-  tc.nb_cA = vb.nb_cA;
-  tc.nb_cB = vb.nb_cB;
+  // coupling-kernel tables for groups of G = 1, 2, 4, 8 consecutive ADOs: the union
+  // of the group's ADOs and their neighbours in ascending order, and the term each
+  // member contributes to each ADO of the group (same float values as the FP32
+  // coupling lists: (float) of the FP64 model entries)
+  for (int q = 0; q < 4; ++q) {
+    const int G = 1 << q;
+    const int ngroups = (M.n_ado + G - 1) / G;
+    std::vector<int> uoff(1, 0), uidx;
+    std::vector<float4> desc;
+    for (int g = 0; g < ngroups; ++g) {
+      std::map<int, std::vector<float4>> terms;   // member -> term per ADO of the group
+      const float4 none = make_float4(0.f, 0.f, bits_as_float(-2), 0.f);
+      for (int k = 0; k < G && g * G + k < M.n_ado; ++k) {
+        const int n = g * G + k;
+        auto slot = [&](int m) -> float4 & {
+          auto &v = terms[m];
+          if (v.empty()) v.assign(G, none);
+          return v[k];
+        };
+        slot(n) = make_float4((float)M.decay[n], 0.f, bits_as_float(-1), 0.f);
+        for (int sm = 0; sm < M.n_modes; ++sm)
+          for (int e = M.nb_off[(size_t)n * M.n_modes + sm]; e < M.nb_off[(size_t)n * M.n_modes + sm + 1]; ++e)
+            slot(M.nb_idx[e]) = make_float4((float)M.nb_cA[e], (float)M.nb_cB[e], bits_as_float(sm), 0.f);
+      }
+      for (auto &kv : terms) {
+        uidx.push_back(kv.first);
+        desc.insert(desc.end(), kv.second.begin(), kv.second.end());
+      }
+      uoff.push_back((int)uidx.size());
+    }
+    void *pu = nullptr, *pi = nullptr, *pd = nullptr;
+    if (device_malloc(&pu, uoff.size() * 4) != cudaSuccess) throw DeviceOom();
+    allocs.push_back(pu);
+    if (device_malloc(&pi, std::max<size_t>(uidx.size(), 1) * 4) != cudaSuccess) throw DeviceOom();
+    allocs.push_back(pi);
+    if (device_malloc(&pd, std::max<size_t>(desc.size(), 1) * sizeof(float4)) != cudaSuccess) throw DeviceOom();
+    allocs.push_back(pd);
+    cudaMemcpy(pu, uoff.data(), uoff.size() * 4, cudaMemcpyHostToDevice);
+    if (!uidx.empty()) cudaMemcpy(pi, uidx.data(), uidx.size() * 4, cudaMemcpyHostToDevice);
+    if (!desc.empty()) cudaMemcpy(pd, desc.data(), desc.size() * sizeof(float4), cudaMemcpyHostToDevice);
+    tc.vt_uoff[q] = (const int *)pu;
+    tc.vt_uidx[q] = (const int *)pi;
+    tc.vt_desc[q] = (const float4 *)pd;
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&tc.sms, cudaDevAttrMultiProcessorCount, dev);
@@ -715,22 +809,40 @@ void tc_build(TcOperators &tc, const Model &M, const VbModel &vb, std::vector<vo
 bool tc_supported(const TcOperators &tc) { return tc.ready; }
 
 // Shapes of the coupling kernel the autotuner chooses from: rows per thread x
-// row groups (128 threads each) per block.
+// row groups (128 threads each) per block x consecutive ADOs per block.
 struct VtShape {
-  int rpt, groups;
+  int rpt, groups, ados;
+  bool pf;    // bulk L2 prefetch of the block's source bands at its start
+  bool two;   // two union members' loads in flight per thread
 };
-constexpr VtShape kVtShapes[] = {{8, 2}, {4, 2}, {4, 4}, {8, 1}, {16, 1}, {8, 4}};
+constexpr VtShape kVtShapes[] = {
+    {8, 2, 1, false, false}, {4, 2, 1, false, false}, {8, 1, 1, false, false}, {4, 2, 2, false, false},
+    {4, 2, 4, false, false}, {4, 1, 4, false, false}, {2, 2, 8, false, false}, {4, 1, 8, false, false},
+    {8, 1, 1, true, false},  {4, 2, 1, true, false},  {8, 2, 1, true, false},  {4, 2, 4, true, false},
+    {16, 1, 1, true, false}, {4, 1, 1, true, false},  {8, 1, 1, true, true},   {4, 1, 1, true, true},
+    {4, 2, 1, true, true}};
 constexpr int kVtShapeCount = (int)(sizeof(kVtShapes) / sizeof(kVtShapes[0]));
 
 static void launch_vterm(int shape, int64_t blocks, const TcArgs &a, cudaStream_t st) {
   const unsigned g = (unsigned)blocks;
   switch (shape) {
-    case 1: vterm_kernel<4, 2><<<g, 256, 0, st>>>(a); break;
-    case 2: vterm_kernel<4, 4><<<g, 512, 0, st>>>(a); break;
-    case 3: vterm_kernel<8, 1><<<g, 128, 0, st>>>(a); break;
-    case 4: vterm_kernel<16, 1><<<g, 128, 0, st>>>(a); break;
-    case 5: vterm_kernel<8, 4><<<g, 512, 0, st>>>(a); break;
-    default: vterm_kernel<8, 2><<<g, 256, 0, st>>>(a); break;
+    case 1: vterm_kernel<4, 2, 1, false, false><<<g, 256, 0, st>>>(a); break;
+    case 2: vterm_kernel<8, 1, 1, false, false><<<g, 128, 0, st>>>(a); break;
+    case 3: vterm_kernel<4, 2, 2, false, false><<<g, 256, 0, st>>>(a); break;
+    case 4: vterm_kernel<4, 2, 4, false, false><<<g, 256, 0, st>>>(a); break;
+    case 5: vterm_kernel<4, 1, 4, false, false><<<g, 128, 0, st>>>(a); break;
+    case 6: vterm_kernel<2, 2, 8, false, false><<<g, 256, 0, st>>>(a); break;
+    case 7: vterm_kernel<4, 1, 8, false, false><<<g, 128, 0, st>>>(a); break;
+    case 8: vterm_kernel<8, 1, 1, true, false><<<g, 128, 0, st>>>(a); break;
+    case 9: vterm_kernel<4, 2, 1, true, false><<<g, 256, 0, st>>>(a); break;
+    case 10: vterm_kernel<8, 2, 1, true, false><<<g, 256, 0, st>>>(a); break;
+    case 11: vterm_kernel<4, 2, 4, true, false><<<g, 256, 0, st>>>(a); break;
+    case 12: vterm_kernel<16, 1, 1, true, false><<<g, 128, 0, st>>>(a); break;
+    case 13: vterm_kernel<4, 1, 1, true, false><<<g, 128, 0, st>>>(a); break;
+    case 14: vterm_kernel<8, 1, 1, true, true><<<g, 128, 0, st>>>(a); break;
+    case 15: vterm_kernel<4, 1, 1, true, true><<<g, 128, 0, st>>>(a); break;
+    case 16: vterm_kernel<4, 2, 1, true, true><<<g, 256, 0, st>>>(a); break;
+    default: vterm_kernel<8, 2, 1, false, false><<<g, 256, 0, st>>>(a); break;
   }
 }
 
@@ -739,7 +851,7 @@ static void launch_vterm(int shape, int64_t blocks, const TcArgs &a, cudaStream_
 // selects the Horner stage's buffers (w, out, tpart, max_in, max_out) of each
 // set.  Returns the coupling kernel's block count.
 static int64_t tc_stage_sets(const std::vector<TcRk4Set> &sets, int which, float alpha, int shape, cudaStream_t st) {
-  const int rows = kVtShapes[shape].rpt * kVtShapes[shape].groups;
+  const int rows = kVtShapes[shape].rpt * kVtShapes[shape].groups, ados = kVtShapes[shape].ados;
   TcArgs a;
   std::memset(&a, 0, sizeof a);
   a.n_sets = (int)sets.size();
@@ -763,11 +875,11 @@ static int64_t tc_stage_sets(const std::vector<TcRk4Set> &sets, int which, float
     unsigned *mo[4] = {ma, mb, ma, my};
     S.himg = tc.himg;
     S.lam = tc.lam;
-    S.decay = tc.decay;
-    S.nb_off = tc.nb_off;
-    S.nb_idx = tc.nb_idx;
-    S.nb_cA = tc.nb_cA;
-    S.nb_cB = tc.nb_cB;
+    for (int q = 0; q < 4; ++q) {
+      S.vt_uoff[q] = tc.vt_uoff[q];
+      S.vt_uidx[q] = tc.vt_uidx[q];
+      S.vt_desc[q] = tc.vt_desc[q];
+    }
     S.w = w[which];
     S.y = R.y;
     S.out = out[which];
@@ -783,7 +895,7 @@ static int64_t tc_stage_sets(const std::vector<TcRk4Set> &sets, int which, float
     S.vt_begin = blocks;
     const int64_t n = (int64_t)R.branches * tc.n_ado;
     items += n;
-    blocks += n * S.bands;
+    blocks += (int64_t)R.branches * ((tc.n_ado + ados - 1) / ados) * S.bands;
   }
   a.n_items = items;
   if (items == 0) return 0;
@@ -811,6 +923,15 @@ static int64_t total_elements(const std::vector<TcRk4Set> &sets) {
 // y and its item maxima and writes scratch (wa and its maxima) that the RK4
 // step overwrites, so tuning changes no result.  Needs the item maxima of y.
 static std::atomic<int> g_forced_shape{-1};
+
+bool tc_shape_params(int shape, int *rpt, int *groups, int *ados, int *flags) {
+  if (shape < 0 || shape >= kVtShapeCount) return false;
+  if (rpt) *rpt = kVtShapes[shape].rpt;
+  if (groups) *groups = kVtShapes[shape].groups;
+  if (ados) *ados = kVtShapes[shape].ados;
+  if (flags) *flags = (kVtShapes[shape].pf ? 1 : 0) | (kVtShapes[shape].two ? 2 : 0);
+  return true;
+}
 
 bool tc_force_shape(int shape) {
   if (shape < -1 || shape >= kVtShapeCount) return false;

@@ -42,9 +42,11 @@ struct TcOperators {
   float inv_sh = 1.f;             // 1 / (power-of-two scale applied to H')
   const uint4 *himg = nullptr;    // n_hpieces shared-memory images of H' pieces (32 KB each)
   const float *lam = nullptr;     // [n_modes][128] lam_s[digit_s(a)]
-  const double *decay = nullptr;  // [n_ado]
-  const int *nb_off = nullptr, *nb_idx = nullptr;
-  const float *nb_cA = nullptr, *nb_cB = nullptr;
+  // coupling-kernel tables for groups of 1, 2, 4, 8 consecutive ADOs (index log2 of
+  // the group size): union offsets and members, and one term per (member, ADO)
+  const int *vt_uoff[4] = {nullptr, nullptr, nullptr, nullptr};
+  const int *vt_uidx[4] = {nullptr, nullptr, nullptr, nullptr};
+  const float4 *vt_desc[4] = {nullptr, nullptr, nullptr, nullptr};
   int *err = nullptr;             // device error word (bounded waits)
   uint64_t wait_ns = 2000000000ull;  // time limit of each device-side wait
   int sms = 0;
@@ -85,8 +87,12 @@ void tc_rk4_sets(const std::vector<TcRk4Set> &sets, double dt, int64_t nsteps, c
 // the state the launches will see; wa receives scratch.  tc_rk4_sets tunes an
 // untuned size itself when it is not being captured.
 void tc_tune(const std::vector<TcRk4Set> &sets, double dt, cudaStream_t st);
-// Use coupling-kernel shape `shape` (0-5) for every launch instead of the tuned
+// Use coupling-kernel shape `shape` (0-16) for every launch instead of the tuned
 // one, or tune again (-1).  Process-wide; false if shape is out of range.
 bool tc_force_shape(int shape);
+// Rows per thread, row groups of 128 threads, consecutive ADOs per block and the
+// flags (bit 0: L2 prefetch, bit 1: two sources in flight) of coupling-kernel
+// shape `shape`; false if out of range.
+bool tc_shape_params(int shape, int *rpt, int *groups, int *ados, int *flags);
 
 }  // namespace heom

@@ -104,6 +104,8 @@ def lib():
         "heom_state_save": [_P, ct.c_char_p],
         "heom_state_load": [_P, ct.c_char_p],
         "heom_debug_force_tc_shape": [ct.c_int],
+        "heom_get_tc_shape": [_P, ct.c_int64, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
+                              ct.POINTER(ct.c_int)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -463,9 +465,21 @@ def heom_debug_fail_alloc(after):
     lib().heom_debug_fail_alloc(int(after))
 
 
+TC_SHAPES = 17   # coupling-kernel shapes of the tensor-core path
+
+
 def heom_debug_force_tc_shape(shape):
-    """Force the tensor-core path's coupling-kernel shape (0-5), or -1 to tune again."""
+    """Force the tensor-core path's coupling-kernel shape (0-16), or -1 to tune again."""
     _check(lib().heom_debug_force_tc_shape(int(shape)))
+
+
+def heom_get_tc_shape(h, elements):
+    """(rows per thread, row groups, ADOs per block, flags) tuned for `elements`, or None;
+    flags bit 0: bulk L2 prefetch, bit 1: two neighbour sources in flight per thread."""
+    r, g, a, p = ct.c_int(0), ct.c_int(0), ct.c_int(0), ct.c_int(0)
+    if lib().heom_get_tc_shape(h.h, int(elements), ct.byref(r), ct.byref(g), ct.byref(a), ct.byref(p)) != 1:
+        return None
+    return r.value, g.value, a.value, p.value
 
 
 def heom_launch_count():

@@ -331,7 +331,7 @@ def test_tensor_core_coupling_shapes_and_tuning():
     eq = H.heom_equilibrate(h, grid["dt_fs"], grid["t_eq_fs"], 0.0)
     got = []
     try:
-        for shape in range(6):
+        for shape in range(H.TC_SHAPES):
             H.heom_debug_force_tc_shape(shape)
             got.append(H.heom_response_2d(h, eq, grid))
     finally:
@@ -344,9 +344,13 @@ def test_tensor_core_coupling_shapes_and_tuning():
     tuned = [e for e in H.heom_get_tuning(h) if e[0] == 2]
     B = 2 * grid["n1"]
     assert len(tuned) == 1 and tuned[0][1] == B * h.n_ado * h.d * h.d
-    assert tuned[0][2] in (128, 256, 512)
-    assert any(tuned[0][3] == B * h.n_ado * -(-h.d // r) and tuned[0][2] == t for r, t in
-               ((16, 256), (8, 256), (16, 512), (8, 128), (16, 128), (32, 512)))
+    rpt, groups, ados, pf = H.heom_get_tc_shape(h, tuned[0][1])
+    assert (rpt, groups, ados, pf) in ((8, 2, 1, 0), (4, 2, 1, 0), (8, 1, 1, 0), (4, 2, 2, 0), (4, 2, 4, 0),
+                                       (4, 1, 4, 0), (2, 2, 8, 0), (4, 1, 8, 0), (8, 1, 1, 1), (4, 2, 1, 1),
+                                       (8, 2, 1, 1), (4, 2, 4, 1), (16, 1, 1, 1), (4, 1, 1, 1),
+                                       (8, 1, 1, 3), (4, 1, 1, 3), (4, 2, 1, 3))
+    assert tuned[0][2] == 128 * groups
+    assert tuned[0][3] == B * -(-h.n_ado // ados) * -(-h.d // (rpt * groups))
     H.heom_response_2d(h, eq, grid)
     assert [e for e in H.heom_get_tuning(h) if e[0] == 2] == tuned
     _, RIo, RIIo, SCo = OH.spectrum_2d(OM.Problem(model), grid)

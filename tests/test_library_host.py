@@ -110,9 +110,10 @@ def test_new_entry_points_reject_bad_arguments_on_host():
     # a hierarchy that has not propagated has no tuned launch shapes
     assert H.heom_get_tuning(h) == []
     assert L.heom_get_tuning(None, 0, None, None, None, None) == 0
-    # the coupling-kernel shape override takes 0-5, or -1 to tune again
-    assert L.heom_debug_force_tc_shape(6) == -1 and L.heom_debug_force_tc_shape(-2) == -1
-    assert L.heom_debug_force_tc_shape(5) == 0 and L.heom_debug_force_tc_shape(-1) == 0
+    # the coupling-kernel shape override takes 0-16, or -1 to tune again
+    assert L.heom_debug_force_tc_shape(17) == -1 and L.heom_debug_force_tc_shape(-2) == -1
+    assert L.heom_debug_force_tc_shape(16) == 0 and L.heom_debug_force_tc_shape(-1) == 0
+    assert H.heom_get_tc_shape(h, 1) is None
 
 
 def test_c5_batch_sets_are_seeded_and_uneven():
