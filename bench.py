@@ -99,7 +99,7 @@ def algorithmic_costs(model, d, nado, ado_table, nb_counts, prec):
 # 256 branches), keyed by the coupling kernel's shape (rows per thread, row groups,
 # ADOs per block, flags); a shape without a capture of the current kernels reports
 # none.
-TC_STAGE_TRAFFIC_BYTES_PER_ITEM = {}
+TC_STAGE_TRAFFIC_BYTES_PER_ITEM = {(8, 1, 1, 1): 758.2e3}
 
 
 class ClockSampler:
