@@ -154,6 +154,10 @@ heom_status heom_equilibrate(heom_hier *h, double dt_fs, double t_max_fs, double
 heom_status heom_state_create(const heom_hier *h, int branches, int precision, heom_state **out);
 heom_status heom_state_upload(heom_state *s, const double *host);
 heom_status heom_state_download(const heom_state *s, double *host);
+/* The same copy under the name of the hot-path contract's boundary list: host
+ * receives [branches][n_ado][d][d] complex128 (interleaved doubles) in the product
+ * eigenbasis; HEOM_EINVAL for a NULL argument. */
+heom_status heom_state_copy_out(const heom_state *s, double *host);
 int heom_state_branches(const heom_state *s);
 
 /*

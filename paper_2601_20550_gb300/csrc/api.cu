@@ -570,6 +570,8 @@ heom_status heom_state_download(const heom_state *s, double *host) {
   });
 }
 
+heom_status heom_state_copy_out(const heom_state *s, double *host) { return heom_state_download(s, host); }
+
 heom_status heom_propagate(heom_hier *h, heom_state *rho, double dt_fs, int64_t n_steps) {
   if (!h || !rho || n_steps < 0) return fail(HEOM_EINVAL, "bad propagate arguments");
   if (rho->d != h->M.d || rho->n_ado != h->M.n_ado) return fail(HEOM_EINVAL, "state does not match hierarchy");

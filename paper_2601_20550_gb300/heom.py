@@ -77,6 +77,7 @@ def lib():
         "heom_state_create": [_P, ct.c_int, ct.c_int, ct.POINTER(_P)],
         "heom_state_upload": [_P, _D],
         "heom_state_download": [_P, _D],
+        "heom_state_copy_out": [_P, _D],
         "heom_propagate": [_P, _P, ct.c_double, ct.c_int64],
         "heom_kick": [_P, _P, ct.c_int],
         "heom_trace": [_P, _P, ct.c_int, _D],
@@ -241,6 +242,13 @@ def heom_state_upload(s, arr):
 def heom_state_download(s):
     a = np.zeros(s.shape, dtype=np.complex128)
     _check(lib().heom_state_download(s.h, a.ctypes.data_as(_D)))
+    return a
+
+
+def heom_state_copy_out(s):
+    """The state as [branches][n_ado][d][d] complex128 in the product eigenbasis."""
+    a = np.zeros(s.shape, dtype=np.complex128)
+    _check(lib().heom_state_copy_out(s.h, a.ctypes.data_as(_D)))
     return a
 
 

@@ -39,6 +39,7 @@ def test_state_save_load_bit_exact(tmp_path, precision):
     H.heom_propagate(h, s, 0.5, 2)
     H.heom_propagate(h, t, 0.5, 2)
     assert np.array_equal(H.heom_state_download(t), H.heom_state_download(s))
+    assert np.array_equal(H.heom_state_copy_out(t), H.heom_state_download(t))
     # a corrupted file leaves the target untouched; another shape is an argument error
     raw = bytearray(open(p, "rb").read())
     raw[200] ^= 0x40
