@@ -276,8 +276,9 @@ heom_status heom_response_2d_grad(heom_hier *h, const heom_state *rho_eq, const 
  * one coupling-kernel launch (per-set operators and buffers in the launch's
  * descriptor; a CTA reloads H' when its next item belongs to another set).  In
  * both cases results equal those of heom_response_2d per set, bit for bit.
- * Otherwise the sets run one after the other, each with all its branches
- * batched.
+ * Otherwise (mixed precisions, more than 16 tensor-core sets, or a tensor-core
+ * hierarchy named twice) the sets run one after the other, each with all its
+ * branches batched.
  */
 heom_status heom_response_2d_batched(heom_hier *const *hs, const heom_state *const *eqs, int n_sets,
                                      const heom_grid *g, double *R_I, double *R_II, double *S_C);

@@ -282,6 +282,10 @@ heom_status heom_response_2d_batched(heom_hier *const *hs, const heom_state *con
     if (a != HEOM_OK) return a;
     all64 = all64 && hs[i]->M.precision == HEOM_FP64;
     alltc = alltc && hs[i]->M.precision == HEOM_TC;
+    // a tensor-core hierarchy keeps per-item scale workspace for one set at a
+    // time: a batch that names one twice runs set by set
+    for (int j = 0; j < i; ++j)
+      if (hs[j] == hs[i]) alltc = false;
   }
   if (!all64 && !alltc) {
     for (int i = 0; i < n_sets; ++i) {

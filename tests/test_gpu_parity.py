@@ -410,6 +410,19 @@ def test_batched_tensor_core_sets_one_launch():
 
 
 @pytest.mark.gpu
+def test_batched_tensor_core_repeated_hierarchy():
+    """A tensor-core hierarchy named twice in one batch (its scale workspace serves one
+    set at a time) runs set by set and gives the single-set result for both entries."""
+    grid = W.grid(0.5, 4, 5, 4, (0.0,), t_eq_fs=20.0)
+    h = H.heom_build_hierarchy(W.small_three_mode(n=2, depth_L=2), H.TC)
+    eq = H.heom_equilibrate(h, grid["dt_fs"], grid["t_eq_fs"], 0.0)
+    RI, RII, SC = H.heom_response_2d_batched([h, h], [eq, eq], grid)
+    ri, rii, sc = H.heom_response_2d(h, eq, grid)
+    for i in range(2):
+        assert np.array_equal(RI[i], ri) and np.array_equal(RII[i], rii) and np.array_equal(SC[i], sc)
+
+
+@pytest.mark.gpu
 def test_steady_state_krylov():
     """GMRES steady state against the oracle's direct null-vector solve."""
     model = W.harmonic_bo(omega_cm=300.0, n_levels=5, lambda_cm=60.0, gamma_cm=150.0,
