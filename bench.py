@@ -579,8 +579,9 @@ def main():
         pinned = torch.from_numpy(eq_host.view(np.float64)).pin_memory()
         eq_up = H.heom_state_create(h, 1, 0)
         rows = min(args.e2e_rows or e2e_rows, grid["n1"])
-        # warm-up call on one row
-        H.heom_response_2d_rows(h, eq, grid, 0, 1)
+        # warm-up call of the timed size (the first call of a batch size tunes the
+        # coupling kernel's launch shape once; repeated calls reuse it)
+        H.heom_response_2d_rows(h, eq, grid, 0, rows)
         tt = []
         d2h = 0
         for i in range(args.e2e_steps):
