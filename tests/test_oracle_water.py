@@ -9,6 +9,10 @@
         S_C(q, p) = -4 mu01^4 dtau^2 a(q - p0) a(p - p0),
         a(0) = N - 1/2,  a(x != 0 mod N) = -1/2,
     so the printed equations make the 0 -> 1 -> 0 diagonal peak negative.
+  * 1D IR with three and with four levels per mode (Sec. IV.A: the paper finds the two
+    representations' linear absorption spectra nearly identical): the two-mode model's
+    spectra over 1000-4100 cm^-1 correlate to better than 0.99, put their peaks in the
+    same frequency bins and give the same bend/stretch band ratio within 10 %.
   * Table readings (workloads.paper_water_model): the isolated cubic stretch of
     Table (i) has its fundamental at the paper's diagonal stretch peak (about
     3400 cm^-1) and the bend near its 1710 cm^-1; the printed direction of the
@@ -80,3 +84,35 @@ def test_paper_table_readings():
     m3 = W.paper_water_model(3)
     assert len(m3["modes"]) == 3 and len(m3["pairs"]) == 3
     assert M.Problem(W.paper_water_model(3, depth_L=1)).d == 64
+
+
+def linear_spectrum(model, n=256, dt=0.5, m=8):
+    prob = M.Problem(model)
+    rho, _, _ = Hm.equilibrate(prob, dt, t_eq_fs=100.0)
+    R1 = Hm.response_1d(prob, rho, dt, m, n)
+    dtau = dt * m
+    w = np.ones(n)
+    w[0] = 0.5
+    om = np.arange(n) / (n * dtau * C_CM_PER_FS)
+    ph = np.exp(2j * math.pi * np.outer(np.arange(n), np.arange(n)) / n)
+    return om, (dtau * (ph @ (w * R1))).imag
+
+
+def test_three_and_four_levels_give_nearly_the_same_linear_spectrum():
+    spectra = {nl: linear_spectrum(W.paper_water_model(2, n_levels=nl, depth_L=2)) for nl in (3, 4)}
+    om = spectra[3][0]
+    sel = (om > 1000.0) & (om < 4100.0)
+    a, b = spectra[3][1][sel], spectra[4][1][sel]
+    assert np.dot(a, b) / (np.linalg.norm(a) * np.linalg.norm(b)) > 0.99
+
+    def peaks(x):
+        big = np.abs(x) > 0.15 * np.abs(x).max()
+        return [i for i in range(1, len(x) - 1) if big[i] and abs(x[i]) >= abs(x[i - 1]) and abs(x[i]) >= abs(x[i + 1])]
+
+    assert peaks(a) == peaks(b) and len(peaks(a)) >= 1
+    ratio = []
+    for nl in (3, 4):
+        I = spectra[nl][1]
+        ratio.append(I[(om > 1400) & (om < 2000)].sum() / I[(om > 3000) & (om < 3900)].sum())
+    assert ratio[0] > 0 and abs(ratio[0] - ratio[1]) < 0.1 * abs(ratio[1])
+
