@@ -8,6 +8,9 @@
   * HEOM_ENOMEM: the library's device allocations go through one allocator with a
     host-side failure injection (heom_debug_fail_alloc); the entry points that
     need memory report HEOM_ENOMEM and leave the caller's state untouched.
+  * HEOM_ENONFINITE: an equilibrium state holding a NaN carries it through the kicks,
+    the propagation and the traces; the response is checked on the host before the
+    call returns.
 """
 import numpy as np
 import pytest
@@ -92,3 +95,17 @@ def test_allocation_failure_reports_enomem_and_recovers():
     H.heom_state_upload(s2, x)
     H.heom_propagate(h2, s2, 0.5, 3)
     assert rel(H.heom_state_download(s2), OH.propagate(prob, x, 0.5, 3)) < 1e-12
+
+
+def test_nonfinite_response_reported():
+    model = W.small_two_mode(n1=2, n2=2, depth_L=1)
+    h = H.heom_build_hierarchy(model, H.FP64)
+    eq = H.heom_state_create(h, 1, H.FP64)
+    x = np.zeros((1, h.n_ado, h.d, h.d), dtype=np.complex128)
+    x[0, 0] = np.eye(h.d) / h.d
+    x[0, 0, 0, 0] = np.nan
+    H.heom_state_upload(eq, x)
+    with pytest.raises(H.HeomError) as err:
+        H.heom_response_2d(h, eq, W.grid(0.5, 2, 3, 3, (0.0,)))
+    assert err.value.status == -7
+
