@@ -303,6 +303,7 @@ void response_2d_rows_impl(heom_hier *h, const heom_state *eq, const heom_grid *
     // coupling-basis complex64 state): its error would reach every t1 row, and one
     // branch is a small share of the scan's work.
     const int trunk_prec = M.precision == HEOM_TC ? HEOM_FP32 : M.precision;
+    PhaseRange phase("heom: t1 trunk");
     kick_into<R>(h, (const C *)eqR.p, (C *)T.p, 1, 2, st);
     rk4_steps<R>(h, (C *)T.p, (C *)ta.p, (C *)tb.p, 1, dt, (int64_t)(jr0 + j0) * m, st, trunk_prec);
     for (int j = 0; j < nj; ++j) {
@@ -318,6 +319,7 @@ void response_2d_rows_impl(heom_hier *h, const heom_state *eq, const heom_grid *
     for (int oi = 0; oi < nt2; ++oi) {
       const int it = order[oi];
       C *Y = (C *)P1.p, *WA = (C *)P2.p, *WB = (C *)(nsets == 4 ? P3.p : P0.p);
+      phase.next("heom: t2 fork");
       rk4_steps<R>(h, BR, Y, WA, B, dt, n2[it] - t_now, st, M.precision);
       t_now = n2[it];
       kick_into<R>(h, BR, Y, B, 1, st);
@@ -326,6 +328,7 @@ void response_2d_rows_impl(heom_hier *h, const heom_state *eq, const heom_grid *
         tc_tune({TcRk4Set{&h->tc, (float2 *)Y, (float2 *)WA, (float2 *)WB, B}}, dt, st);
       // the t3 scan (n3 samples of m RK4 steps and two traces) is captured once
       // into a CUDA graph and replayed as a single launch
+      phase.next("heom: t3 scan");
       GraphCapture cap(st);
       for (int k = 0; k < n3; ++k) {
         if (k > 0) rk4_steps<R>(h, Y, WA, WB, B, dt, m, st, M.precision);
@@ -575,6 +578,7 @@ heom_status heom_state_copy_out(const heom_state *s, double *host) { return heom
 heom_status heom_propagate(heom_hier *h, heom_state *rho, double dt_fs, int64_t n_steps) {
   if (!h || !rho || n_steps < 0) return fail(HEOM_EINVAL, "bad propagate arguments");
   if (rho->d != h->M.d || rho->n_ado != h->M.n_ado) return fail(HEOM_EINVAL, "state does not match hierarchy");
+  PhaseRange phase("heom: propagate");
   return guarded([&]() -> heom_status {
     stability_check(h, dt_fs);
     ensure_device(h);
@@ -641,6 +645,7 @@ heom_status heom_trace(heom_hier *h, const heom_state *rho, int order, double *o
 
 heom_status heom_equilibrate(heom_hier *h, double dt_fs, double t_max_fs, double tol, heom_state **rho_eq) {
   if (!h || !rho_eq || !(t_max_fs >= 0)) return fail(HEOM_EINVAL, "bad equilibrate arguments");
+  PhaseRange phase("heom: equilibrate");
   *rho_eq = nullptr;
   {
     heom_status e = guarded([&]() -> heom_status {
@@ -727,6 +732,7 @@ heom_status heom_response_2d(heom_hier *h, const heom_state *rho_eq, const heom_
     rows_dispatch(h, rho_eq, g, 0, n1, (double2 *)Rdev.p);
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     check_tc_error(h);
+    PhaseRange phase("heom: 2D DFT");
     const double dtau = g->dt_fs * g->steps_per_sample;
     for (int it = 0; it < nt2; ++it) {
       double2 *RI = (double2 *)Rdev.p + (int64_t)it * 2 * n1 * n3;

@@ -135,6 +135,7 @@ static void response_2d_multi(heom_hier *const *hs, const heom_state *const *eqs
     MultiStep fork, scan;
     multi_step_setup(S, fork, 0, 1, 2, B, st);                       // y = BR, scratch Y, WA
     multi_step_setup(S, scan, 1, 2, nbuf == 4 ? 3 : 0, B, st);       // y = Y, scratch WA, WB
+    PhaseRange phase("heom: t1 trunk (sets)");
     for (int k = 0; k < n_sets; ++k)
       kick_into<double>(S[k].h, (const double2 *)S[k].eq->buf.p, (double2 *)S[k].T->p, 1, 2, st);
     multi_rk4(trunk, n_sets, dt, (int64_t)j0 * m, st);
@@ -153,10 +154,12 @@ static void response_2d_multi(heom_hier *const *hs, const heom_state *const *eqs
     int64_t t_now = 0;
     for (int oi = 0; oi < nt2; ++oi) {
       const int it = order[oi];
+      phase.next("heom: t2 fork (sets)");
       multi_rk4(fork, n_sets, dt, n2[it] - t_now, st);
       t_now = n2[it];
       for (int k = 0; k < n_sets; ++k)
         kick_into<double>(S[k].h, (const double2 *)S[k].P[0]->p, (double2 *)S[k].P[1]->p, B, 1, st);
+      phase.next("heom: t3 scan (sets)");
       GraphCapture cap(st);
       for (int kk = 0; kk < n3; ++kk) {
         if (kk > 0) multi_rk4(scan, n_sets, dt, m, st);
@@ -228,6 +231,7 @@ static void response_2d_multi_tc(heom_hier *const *hs, const heom_state *const *
   for (int j0 = 0; j0 < n1; j0 += J) {
     const int nj = std::min(J, n1 - j0), B = 2 * nj;
     const std::vector<TcRk4Set> fork = bufs(0, 1, 2, B), scan = bufs(1, 2, nbuf == 4 ? 3 : 0, B);
+    PhaseRange phase("heom: t1 trunk (tensor-core sets)");
     for (int k = 0; k < n_sets; ++k) {
       // trunk on the FP32 CUDA-core stage, then the second kick of both pathways
       heom_hier *h = hs[k];
@@ -247,11 +251,13 @@ static void response_2d_multi_tc(heom_hier *const *hs, const heom_state *const *
     int64_t t_now = 0;
     for (int oi = 0; oi < nt2; ++oi) {
       const int it = order[oi];
+      phase.next("heom: t2 fork (tensor-core sets)");
       tc_rk4_sets(fork, dt, n2[it] - t_now, st);
       t_now = n2[it];
       for (int k = 0; k < n_sets; ++k)
         kick_into<float>(hs[k], (const float2 *)S[k].P[0]->p, (float2 *)S[k].P[1]->p, B, 1, st);
       tc_tune(scan, dt, st);   // coupling-kernel shape, once per size, before the capture
+      phase.next("heom: t3 scan (tensor-core sets)");
       GraphCapture cap(st);
       for (int kk = 0; kk < n3; ++kk) {
         if (kk > 0) tc_rk4_sets(scan, dt, m, st);

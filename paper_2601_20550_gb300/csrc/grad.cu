@@ -268,6 +268,7 @@ static void dft2d_adjoint(const double *Sbar, int n1, int n3, double dtau, std::
 
 extern "C" heom_status heom_response_2d_grad(heom_hier *h, const heom_state *rho_eq, const heom_grid *g,
                                              const double *S_ref, int ckpt_every, double *loss, double *dtheta) {
+  PhaseRange phase("heom: adjoint gradient");
   heom_status a = check_response_args(h, rho_eq, g);
   if (a != HEOM_OK) return a;
   if (!S_ref || !loss || !dtheta || ckpt_every < 1) return fail(HEOM_EINVAL, "bad gradient arguments");

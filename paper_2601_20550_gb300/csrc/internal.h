@@ -16,6 +16,7 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "heom2dvs.h"
 #include "kernels.cuh"
@@ -26,6 +27,21 @@ namespace heom {
 
 extern thread_local std::string g_last_error;
 void count_launch(uint64_t n);
+
+// NVTX range over a phase of a call (equilibrate, t1 trunk, t2 fork, t3 scan, DFT,
+// ...); no-ops unless a profiler is attached.  next() closes the current phase and
+// opens the following one; the destructor closes the last (also on an exception).
+class PhaseRange {
+ public:
+  explicit PhaseRange(const char *name) { nvtxRangePushA(name); }
+  ~PhaseRange() { nvtxRangePop(); }
+  void next(const char *name) {
+    nvtxRangePop();
+    nvtxRangePushA(name);
+  }
+  PhaseRange(const PhaseRange &) = delete;
+  PhaseRange &operator=(const PhaseRange &) = delete;
+};
 
 struct Fail {
   heom_status st;

@@ -60,6 +60,7 @@ static void apply_L(heom_hier *h, const double2 *x, double2 *out, int64_t n, cud
 
 extern "C" heom_status heom_steady_state(heom_hier *h, double tol, int restart, int max_iter, double dt_fs,
                                          int steps_per_matvec, heom_state **rho_eq, int *iterations) {
+  PhaseRange phase("heom: steady state");
   if (!h || !rho_eq || !(tol > 0) || restart < 2 || max_iter < 1 || steps_per_matvec < 0)
     return fail(HEOM_EINVAL, "bad steady-state arguments");
   *rho_eq = nullptr;
