@@ -423,6 +423,22 @@ def test_batched_tensor_core_repeated_hierarchy():
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("precision", [0, 2])
+def test_repeated_calls_are_bitwise_identical(precision):
+    """Every reduction (traces, maxima, Fourier sums) runs in a fixed order and no result
+    depends on a launch shape, so a repeated call (the second one with the shapes the
+    first one tuned) returns the same bits."""
+    model = W.small_two_mode(n1=3, n2=3, depth_L=2)
+    grid = W.grid(0.5, 4, 6, 5, (0.0, 4.0), t_eq_fs=20.0)
+    h = H.heom_build_hierarchy(model, precision)
+    eq = H.heom_equilibrate(h, grid["dt_fs"], grid["t_eq_fs"], 0.0)
+    first = H.heom_response_2d(h, eq, grid)
+    second = H.heom_response_2d(h, eq, grid)
+    for a, b in zip(first, second):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.gpu
 def test_steady_state_krylov():
     """GMRES steady state against the oracle's direct null-vector solve."""
     model = W.harmonic_bo(omega_cm=300.0, n_levels=5, lambda_cm=60.0, gamma_cm=150.0,
