@@ -16,7 +16,14 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#if __has_include(<nvtx3/nvToolsExt.h>)
 #include <nvtx3/nvToolsExt.h>
+#define HEOM_NVTX_PUSH(name) nvtxRangePushA(name)
+#define HEOM_NVTX_POP() nvtxRangePop()
+#else  // a toolkit without the NVTX headers: phase ranges compile to nothing
+#define HEOM_NVTX_PUSH(name) ((void)(name))
+#define HEOM_NVTX_POP() ((void)0)
+#endif
 
 #include "heom2dvs.h"
 #include "kernels.cuh"
@@ -33,11 +40,11 @@ void count_launch(uint64_t n);
 // opens the following one; the destructor closes the last (also on an exception).
 class PhaseRange {
  public:
-  explicit PhaseRange(const char *name) { nvtxRangePushA(name); }
-  ~PhaseRange() { nvtxRangePop(); }
+  explicit PhaseRange(const char *name) { HEOM_NVTX_PUSH(name); }
+  ~PhaseRange() { HEOM_NVTX_POP(); }
   void next(const char *name) {
-    nvtxRangePop();
-    nvtxRangePushA(name);
+    HEOM_NVTX_POP();
+    HEOM_NVTX_PUSH(name);
   }
   PhaseRange(const PhaseRange &) = delete;
   PhaseRange &operator=(const PhaseRange &) = delete;
