@@ -227,12 +227,11 @@ heom_status heom_steady_state(heom_hier *h, double tol, int restart, int max_ite
  * persistent 544-thread CTA per SM, bounded by its shared and tensor memory);
  * the coupling kernel that follows it is tuned over seventeen shapes (2, 4, 8 or
  * 16 rows per thread x 1 or 2 groups of 128 threads x 1, 2, 4 or 8 consecutive
- * ADOs per block, with or without a bulk L2 prefetch of the block's sources and
- * two neighbour sources in flight per thread; see
- * heom_get_tc_shape) by timing whole first RK4 stages,
- * before the response scan's graph capture or on the first uncaptured
- * propagation of a size; a batched call keeps its entry in its first
- * hierarchy.  For kind 2, block is threads per block and grid the coupling
+ * ADOs per block, some with a bulk L2 prefetch of the block's sources and some
+ * also with two neighbour sources in flight per thread; heom_get_tc_shape
+ * reports the choice) by timing whole first RK4 stages, before the response
+ * scan's graph capture or on the first uncaptured propagation of a size; a
+ * batched call keeps its entry in its first hierarchy.  For kind 2, block is threads per block and grid the coupling
  * kernel's blocks per launch.  elements = state elements of the launch (all
  * branches, ADOs and sets).  Returns the number of tuned (kind, elements)
  * entries of h and copies up to cap of them (any pointer may be NULL).
