@@ -54,7 +54,11 @@ def response_2d_sharded(h, rho_eq, grid, dist=None, rows_fn=None, group=None):
     if rows_fn is None:
         def rows_fn(a, b):
             return H.heom_response_2d_rows(h, rho_eq, grid, a, b)
-    RI, RII = rows_fn(j0, j1)
+    if j1 > j0:
+        RI, RII = rows_fn(j0, j1)
+    else:   # more ranks than t1 rows: this rank only takes part in the gather
+        RI = np.zeros((len(grid["t2_fs"]), 0, grid["n3"]), dtype=np.complex128)
+        RII = np.zeros_like(RI)
     if world > 1:
         RI, RII = gather_rows(RI, RII, grid["n1"], world, rank, dist, group)
     return RI, RII
