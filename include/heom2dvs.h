@@ -428,6 +428,10 @@ void heom_debug_fail_alloc(int64_t after);
  */
 heom_status heom_debug_force_tc_shape(int shape);
 
+/* Number of coupling-kernel shapes of the tensor-core path (17; shapes 0 .. count - 1
+ * as listed for heom_debug_force_tc_shape).  No device work. */
+int heom_tc_shape_count(void);
+
 /*
  * The coupling-kernel shape the autotuner chose for tensor-core launches over
  * `elements` state elements (the kind-2 entries of heom_get_tuning): rows per

@@ -916,6 +916,8 @@ void heom_debug_fail_alloc(int64_t after) { g_alloc_budget.store(after < 0 ? -1 
 
 heom_status heom_debug_force_tc_shape(int shape) { return tc_force_shape(shape) ? HEOM_OK : HEOM_EINVAL; }
 
+int heom_tc_shape_count(void) { return tc_shape_count(); }
+
 int heom_get_tc_shape(const heom_hier *h, int64_t elements, int *rows_per_thread, int *row_groups,
                       int *ados_per_block, int *flags) {
   if (!h) return 0;

@@ -933,6 +933,8 @@ bool tc_shape_params(int shape, int *rpt, int *groups, int *ados, int *flags) {
   return true;
 }
 
+int tc_shape_count() { return kVtShapeCount; }
+
 bool tc_force_shape(int shape) {
   if (shape < -1 || shape >= kVtShapeCount) return false;
   g_forced_shape.store(shape);

@@ -90,6 +90,8 @@ void tc_tune(const std::vector<TcRk4Set> &sets, double dt, cudaStream_t st);
 // Use coupling-kernel shape `shape` (0-16) for every launch instead of the tuned
 // one, or tune again (-1).  Process-wide; false if shape is out of range.
 bool tc_force_shape(int shape);
+// Number of coupling-kernel shapes (valid shapes are 0 .. count - 1).
+int tc_shape_count();
 // Rows per thread, row groups of 128 threads, consecutive ADOs per block and the
 // flags (bit 0: L2 prefetch, bit 1: two sources in flight) of coupling-kernel
 // shape `shape`; false if out of range.

@@ -105,6 +105,7 @@ def lib():
         "heom_state_save": [_P, ct.c_char_p],
         "heom_state_load": [_P, ct.c_char_p],
         "heom_debug_force_tc_shape": [ct.c_int],
+        "heom_tc_shape_count": [],
         "heom_get_tc_shape": [_P, ct.c_int64, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
                               ct.POINTER(ct.c_int)],
     }
@@ -473,7 +474,9 @@ def heom_debug_fail_alloc(after):
     lib().heom_debug_fail_alloc(int(after))
 
 
-TC_SHAPES = 17   # coupling-kernel shapes of the tensor-core path
+def heom_tc_shape_count():
+    """Number of coupling-kernel shapes of the tensor-core path (valid: 0 .. count - 1)."""
+    return int(lib().heom_tc_shape_count())
 
 
 def heom_debug_force_tc_shape(shape):

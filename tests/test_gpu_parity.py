@@ -331,7 +331,7 @@ def test_tensor_core_coupling_shapes_and_tuning():
     eq = H.heom_equilibrate(h, grid["dt_fs"], grid["t_eq_fs"], 0.0)
     got = []
     try:
-        for shape in range(H.TC_SHAPES):
+        for shape in range(H.heom_tc_shape_count()):
             H.heom_debug_force_tc_shape(shape)
             got.append(H.heom_response_2d(h, eq, grid))
     finally:

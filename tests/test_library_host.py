@@ -111,9 +111,11 @@ def test_new_entry_points_reject_bad_arguments_on_host():
     assert H.heom_get_tuning(h) == []
     assert L.heom_get_tuning(None, 0, None, None, None, None) == 0
     assert L.heom_state_copy_out(None, None) == -1
-    # the coupling-kernel shape override takes 0-16, or -1 to tune again
-    assert L.heom_debug_force_tc_shape(17) == -1 and L.heom_debug_force_tc_shape(-2) == -1
-    assert L.heom_debug_force_tc_shape(16) == 0 and L.heom_debug_force_tc_shape(-1) == 0
+    # the coupling-kernel shape override takes 0 .. count - 1, or -1 to tune again
+    count = H.heom_tc_shape_count()
+    assert count == 17
+    assert L.heom_debug_force_tc_shape(count) == -1 and L.heom_debug_force_tc_shape(-2) == -1
+    assert L.heom_debug_force_tc_shape(count - 1) == 0 and L.heom_debug_force_tc_shape(-1) == 0
     assert H.heom_get_tc_shape(h, 1) is None
 
 
