@@ -13,6 +13,8 @@
     representations' linear absorption spectra nearly identical): the two-mode model's
     spectra over 1000-4100 cm^-1 correlate to better than 0.99, put their peaks in the
     same frequency bins and give the same bend/stretch band ratio within 10 %.
+  * The workload's table constants equal the numbers printed in Sec. IV's Tables (i),
+    (ii) and FitAll2, kept as text in tests/golden/paper_water_tables.txt.
   * Table readings (workloads.paper_water_model): the isolated cubic stretch of
     Table (i) has its fundamental at the paper's diagonal stretch peak (about
     3400 cm^-1) and the bend near its 1710 cm^-1; the printed direction of the
@@ -116,3 +118,30 @@ def test_three_and_four_levels_give_nearly_the_same_linear_spectrum():
         ratio.append(I[(om > 1400) & (om < 2000)].sum() / I[(om > 3000) & (om < 3900)].sum())
     assert ratio[0] > 0 and abs(ratio[0] - ratio[1]) < 0.1 * abs(ratio[1])
 
+
+
+def read_golden_tables():
+    """tests/golden/paper_water_tables.txt: the numbers of Sec. IV's Tables (i), (ii), FitAll2."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "paper_water_tables.txt")
+    modes, pairs, omega0 = {"i": [], "ii": []}, {"i": [], "ii": []}, None
+    for line in open(path):
+        f = line.split()
+        if not f or f[0].startswith("#"):
+            continue
+        if f[0] == "omega_0":
+            omega0 = float(f[1])
+        elif f[0] == "mode":
+            modes[f[1]].append(tuple(float(x) for x in f[3:]))
+        elif f[0] == "pair":
+            pairs[f[1]].append(tuple(float(x) for x in f[3:]))
+    return omega0, modes, pairs
+
+
+def test_workload_tables_match_the_printed_values():
+    omega0, modes, pairs = read_golden_tables()
+    assert omega0 == W.PAPER_OMEGA0_CM
+    assert [tuple(r) for r in W.PAPER_TABLE_I] == modes["i"]
+    assert [tuple(r) for r in W.PAPER_TABLE_II] == modes["ii"]
+    assert [W.PAPER_TABLE_I_PAIRS[k] for k in sorted(W.PAPER_TABLE_I_PAIRS)] == pairs["i"]
+    assert [W.PAPER_FITALL2[k] for k in sorted(W.PAPER_FITALL2)] == pairs["ii"]
