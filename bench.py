@@ -96,10 +96,10 @@ def algorithmic_costs(model, d, nado, ado_table, nb_counts, prec):
 # Measured DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) per work item
 # (one ADO of one branch) of one RK4 stage of the tensor-core path: one ncu capture
 # of a 4-branch c3 case, scaled per item (the per-branch working set is the same at
-# 256 branches), keyed by the coupling kernel's shape (rows per thread, row groups,
-# ADOs per block, flags); a shape without a capture of the current kernels reports
-# none.
-TC_STAGE_TRAFFIC_BYTES_PER_ITEM = {(8, 1, 1, 1): 758.2e3}
+# 256 branches), keyed by the stage kernels' source tag (heom_source_tag: any edit of
+# their source gives another tag) and the coupling kernel's shape (rows per thread,
+# row groups, ADOs per block, flags).  A build or shape without a capture reports none.
+TC_STAGE_TRAFFIC_BYTES_PER_ITEM = {("004539086727f616", (8, 1, 1, 1)): 758.2e3}
 
 
 class ClockSampler:
@@ -502,7 +502,9 @@ def main():
                                                  "ados_per_block": shape[2], "l2_prefetch": shape[3] & 1,
                                                  "two_sources_in_flight": shape[3] >> 1,
                                                  "threads": tuned[0][2], "blocks": tuned[0][3]}
-                per_item = TC_STAGE_TRAFFIC_BYTES_PER_ITEM.get(tuple(shape))
+                tag = H.heom_source_tag()
+                roof["kernel_source_tag"] = tag
+                per_item = TC_STAGE_TRAFFIC_BYTES_PER_ITEM.get((tag, tuple(shape)))
                 if per_item and cfg == "c3":
                     roof["traffic"] = per_item * B * nado
 

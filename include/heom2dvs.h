@@ -432,6 +432,12 @@ heom_status heom_debug_force_tc_shape(int shape);
  * as listed for heom_debug_force_tc_shape).  No device work. */
 int heom_tc_shape_count(void);
 
+/* Tag of the tensor-core stage kernels' source: the first 16 hex digits of the
+ * SHA-256 of tc_stage.cu and tc_stage.h, computed when the library is built, so
+ * that a stored measurement (a DRAM-traffic capture) can be matched to the kernels
+ * it was taken on.  Static string; no device work. */
+const char *heom_source_tag(void);
+
 /*
  * The coupling-kernel shape the autotuner chose for tensor-core launches over
  * `elements` state elements (the kind-2 entries of heom_get_tuning): rows per

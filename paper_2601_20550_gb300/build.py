@@ -4,6 +4,7 @@ Each translation unit is compiled in parallel, then linked into one shared
 library next to this file.  Run as ``python -m paper_2601_20550_gb300.build``.
 """
 import concurrent.futures as cf
+import hashlib
 import os
 import shutil
 import subprocess
@@ -25,11 +26,23 @@ def nvcc():
     raise RuntimeError("nvcc not found")
 
 
+def stage_source_tag():
+    """First 16 hex digits of the SHA-256 of the tensor-core stage kernels' sources
+    (tc_stage.cu, tc_stage.h); the library reports it (heom_source_tag) so that a
+    stored measurement can be matched to the kernels it was taken on."""
+    h = hashlib.sha256()
+    for name in ("tc_stage.cu", "tc_stage.h"):
+        with open(os.path.join(CSRC, name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def compile_one(src, verbose=False):
     obj = os.path.join(BUILD, src + ".o")
     path = os.path.join(CSRC, src)
     cmd = [nvcc(), "-c", path, "-o", obj, "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
-           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-lineinfo"] + ARCH
+           "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-lineinfo",
+           '-DHEOM_TC_STAGE_TAG="%s"' % stage_source_tag()] + ARCH
     if src.endswith(".cpp"):
         cmd += ["-x", "c++"]
     if verbose:

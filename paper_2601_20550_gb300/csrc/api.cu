@@ -918,6 +918,11 @@ heom_status heom_debug_force_tc_shape(int shape) { return tc_force_shape(shape) 
 
 int heom_tc_shape_count(void) { return tc_shape_count(); }
 
+#ifndef HEOM_TC_STAGE_TAG
+#define HEOM_TC_STAGE_TAG "unknown"
+#endif
+const char *heom_source_tag(void) { return HEOM_TC_STAGE_TAG; }
+
 int heom_get_tc_shape(const heom_hier *h, int64_t elements, int *rows_per_thread, int *row_groups,
                       int *ados_per_block, int *flags) {
   if (!h) return 0;

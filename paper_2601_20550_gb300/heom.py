@@ -119,6 +119,7 @@ def lib():
     L.heom_free_state.restype = None
     L.heom_last_error.restype = ct.c_char_p
     L.heom_launch_count.restype = ct.c_uint64
+    L.heom_source_tag.restype = ct.c_char_p
     L.heom_state_device_ptr.argtypes = [_P]
     L.heom_state_device_ptr.restype = _P
     L.heom_state_branches.argtypes = [_P]
@@ -472,6 +473,11 @@ def heom_set_wait_limit_ns(h, ns):
 def heom_debug_fail_alloc(after):
     """Make device allocations fail after `after` more successes (after < 0: off)."""
     lib().heom_debug_fail_alloc(int(after))
+
+
+def heom_source_tag():
+    """SHA-256 tag (16 hex digits) of the tensor-core stage kernels' source the library was built from."""
+    return lib().heom_source_tag().decode()
 
 
 def heom_tc_shape_count():

@@ -162,3 +162,17 @@ def test_unstable_step_rejected_before_any_device_work():
     assert L.heom_equilibrate(h.h, 10.0, 100.0, 0.0, ct.byref(out)) == -4 and not out.value
     # a stable step passes the pre-check (and then needs the device)
     assert L.heom_propagate_dev(h.h, p, p, p, 1, 0, 0.5, 0, None) != -4
+
+
+def test_source_tag_names_the_stage_kernels_source():
+    """heom_source_tag is the SHA-256 prefix of the stage kernels' sources the library was
+    built from, so a stored traffic capture matches only the kernels it measured."""
+    import hashlib
+    import os
+    csrc = os.path.join(os.path.dirname(H.__file__), "csrc")
+    h = hashlib.sha256()
+    for name in ("tc_stage.cu", "tc_stage.h"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
+    assert H.heom_source_tag() == h.hexdigest()[:16]
+
