@@ -15,6 +15,16 @@
     operators are c-numbers).
   * P7 truncation: the c1 spectrum converges monotonically in the hierarchy depth
     and in the number of Pade terms.
+  * Sec. II.A: linear-linear coupling relaxes, square-linear coupling dephases.  On
+    the three lowest harmonic levels (where q^2 has no element between |1> and another
+    kept level) an SL-coupled mode keeps the population of |1> exactly while the
+    0-1 coherence decays; an LL-coupled mode relaxes |1> towards |0>.
+  * Sec. II.C and III: the vibrational quanta are far above kT, so the equilibrium is
+    the ground state, and the paper notes that such modes need a larger low-temperature
+    correction.  The hierarchy's null vector shows both: for two modes of 3400 and 1650
+    cm^-1 at 300 K its ground-state population goes 1.41, 1.05, 1.006, 1.0001 for 1-4
+    Pade terms (one term leaves a non-positive "equilibrium"), converging on the ground
+    state.
 """
 import math
 
@@ -181,3 +191,40 @@ def test_depth_and_pade_convergence():
     dK = [np.abs(S[i + 1] - S[i]).max() / np.abs(S[i + 1]).max() for i in range(3)]
     assert all(dK[i + 1] < 0.2 * dK[i] for i in range(2)), dK
     assert dK[-1] < 1e-5
+
+
+def _harmonic_three_level(vll, vsl):
+    md = W.mode("cubic", 1000.0, g3_cm=0.0, n_levels=3, n_prim=3, lambda_cm=50.0, gamma_cm=500.0,
+                V_LL=vll, V_SL=vsl, mu1=1.0)
+    return M.Problem({"modes": [md], "pairs": [], "T_K": 300.0, "depth_L": 4})
+
+
+def _evolve(prob, rho0, t_fs=400.0, dt=0.5):
+    rho = Hm.initial_state(prob)
+    rho[:] = 0
+    rho[0, 0] = rho0
+    return Hm.propagate(prob, rho, dt, int(t_fs / dt))[0, 0]
+
+
+def test_linear_coupling_relaxes_square_linear_dephases():
+    pop1 = np.zeros((3, 3), dtype=complex)
+    pop1[1, 1] = 1.0
+    v = np.array([1.0, 1.0, 0.0]) / math.sqrt(2.0)
+    coh = np.outer(v, v).astype(complex)
+    ll, sl = _harmonic_three_level(1.0, 0.0), _harmonic_three_level(0.0, 1.0)
+    assert _evolve(ll, pop1)[1, 1].real < 0.5                 # LL: |1> relaxes
+    assert abs(_evolve(sl, pop1)[1, 1].real - 1.0) < 1e-9     # SL: |1> keeps its population
+    assert abs(_evolve(sl, coh)[1, 0]) < 0.8 * 0.5            # ... while the 0-1 coherence decays
+
+
+def test_low_temperature_correction_restores_the_ground_state():
+    dev, mineig = [], []
+    for K in (1, 2, 3, 4):
+        prob = M.Problem(W.small_two_mode(n1=3, n2=2, depth_L=2, K_pade=K))
+        rho0 = Hm.steady_state(prob)[0, 0]
+        assert abs(np.trace(rho0) - 1.0) < 1e-10
+        dev.append(abs(rho0[0, 0].real - 1.0))
+        mineig.append(np.linalg.eigvalsh(0.5 * (rho0 + rho0.conj().T)).min())
+    assert all(a > b for a, b in zip(dev, dev[1:]))      # monotone in the Pade order
+    assert dev[0] > 0.1 and mineig[0] < -0.1               # one term: far from a density matrix
+    assert dev[-1] < 1e-3 and mineig[-1] > -1e-3           # four terms: the ground state
