@@ -432,6 +432,12 @@ heom_status heom_debug_force_tc_shape(int shape);
  * as listed for heom_debug_force_tc_shape).  No device work. */
 int heom_tc_shape_count(void);
 
+/* Parameters of coupling-kernel shape `shape` (0 .. count - 1): rows per thread,
+ * row groups of 128 threads, consecutive ADOs per block, and flags as for
+ * heom_get_tc_shape.  Non-NULL outputs are filled; HEOM_EINVAL out of range. */
+heom_status heom_tc_shape_params(int shape, int *rows_per_thread, int *row_groups, int *ados_per_block,
+                                 int *flags);
+
 /* Tag of the tensor-core stage kernels' source: the first 16 hex digits of the
  * SHA-256 of tc_stage.cu and tc_stage.h, computed when the library is built, so
  * that a stored measurement (a DRAM-traffic capture) can be matched to the kernels

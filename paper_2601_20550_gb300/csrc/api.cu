@@ -918,6 +918,11 @@ heom_status heom_debug_force_tc_shape(int shape) { return tc_force_shape(shape) 
 
 int heom_tc_shape_count(void) { return tc_shape_count(); }
 
+heom_status heom_tc_shape_params(int shape, int *rows_per_thread, int *row_groups, int *ados_per_block,
+                                 int *flags) {
+  return tc_shape_params(shape, rows_per_thread, row_groups, ados_per_block, flags) ? HEOM_OK : HEOM_EINVAL;
+}
+
 #ifndef HEOM_TC_STAGE_TAG
 #define HEOM_TC_STAGE_TAG "unknown"
 #endif

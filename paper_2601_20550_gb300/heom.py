@@ -106,6 +106,8 @@ def lib():
         "heom_state_load": [_P, ct.c_char_p],
         "heom_debug_force_tc_shape": [ct.c_int],
         "heom_tc_shape_count": [],
+        "heom_tc_shape_params": [ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
+                                 ct.POINTER(ct.c_int)],
         "heom_get_tc_shape": [_P, ct.c_int64, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int),
                               ct.POINTER(ct.c_int)],
     }
@@ -478,6 +480,13 @@ def heom_debug_fail_alloc(after):
 def heom_source_tag():
     """SHA-256 tag (16 hex digits) of the tensor-core stage kernels' source the library was built from."""
     return lib().heom_source_tag().decode()
+
+
+def heom_tc_shape_params(shape):
+    """(rows per thread, row groups, ADOs per block, flags) of coupling-kernel shape `shape`."""
+    r, g, a, f = ct.c_int(0), ct.c_int(0), ct.c_int(0), ct.c_int(0)
+    _check(lib().heom_tc_shape_params(int(shape), ct.byref(r), ct.byref(g), ct.byref(a), ct.byref(f)))
+    return r.value, g.value, a.value, f.value
 
 
 def heom_tc_shape_count():
