@@ -14,6 +14,10 @@ sizes and on several parameter sets concatenated in one launch:
 
 The union lists are built here from the hierarchy's own neighbour relation (each
 ADO with its up- and down-neighbours), the definition the library's tables follow.
+
+The tensor-core kernel's producer and epilogue thread mappings are replayed too:
+every element of a d x d item (d <= 128) lands exactly once, at its 128-byte-swizzle
+offset inside its 64 KB operand tile, and every element of tpart is stored once.
 """
 import itertools
 
@@ -146,3 +150,44 @@ def test_coupling_kernel_indexing(shape):
         sets.append((d, n_ado, branches, nbs))
     for cnt in replay(sets, rpt, groups, G, flags & 1):
         assert (cnt == 1).all()
+
+
+def sw128(r, c, colblock_stride):
+    """Byte offset of FP16 element (r, c) in a tile of 64-column blocks, 128-byte rows,
+    16-byte chunks XOR-swizzled by the row mod 8 (the UMMA 128B-swizzle layout)."""
+    return (c >> 6) * colblock_stride + r * 128 + ((((c & 63) >> 3) ^ (r & 7)) << 4) + ((c & 63) * 2 & 15)
+
+
+@pytest.mark.parametrize("d", [1, 6, 27, 64, 125, 128])
+def test_tensor_core_producer_and_epilogue_mapping(d):
+    """The tensor-core kernel's 384 producer threads (column pair 2 cp, rows r0 + 6 g,
+    g < 24, offsets row_ofs[g mod 4] + 3072 (g div 4)) write every element of a d x d
+    item exactly once at its swizzled offset (real half; the imaginary half adds 16384),
+    inside one 64 KB tile; the 128 epilogue lanes (column b) with row blocks of 16 store
+    every element of tpart exactly once."""
+    kZZ = 65536
+    written = np.zeros((d, d), dtype=np.int64)
+    for tid in range(384):
+        cp, r0 = tid & 63, tid >> 6
+        c = 2 * cp
+        cc = c & 63
+        row_ofs = [(c >> 6) * (kZZ // 2) + (r0 + 6 * u) * 128 + ((((cc >> 3) ^ ((r0 + 6 * u) & 7))) << 4)
+                   + ((cc * 2) & 15) for u in range(4)]
+        for g in range(24):
+            a = r0 + 6 * g
+            if not (c < d and a < d):
+                continue
+            o = row_ofs[g & 3] + 3072 * (g >> 2)
+            assert o == sw128(a, c, kZZ // 2) and o + 16384 + 4 <= kZZ and o % 4 == 0
+            assert sw128(a, c + 1, kZZ // 2) == o + 2           # the half2 holds columns c, c + 1
+            written[a, c] += 1
+            if c + 1 < d:
+                written[a, c + 1] += 1
+    assert (written == 1).all()
+    stored = np.zeros((d, d), dtype=np.int64)
+    for b in range(128):
+        for a0 in range(0, d, 16):
+            for jj in range(16):
+                if b < d and a0 + jj < d:
+                    stored[a0 + jj, b] += 1
+    assert (stored == 1).all()
