@@ -17,6 +17,12 @@ Pins (tests/test_oracle_model.py):
     for V_SL != 0 against ladder-operator matrix elements (V^2 squared in a larger
     basis); the square-linear pure-dephasing closed form; the quadratic and
     cross-mode dipole terms through the zero-bath linear response.
+  * Physics (tests/test_oracle_physics.py): LL coupling relaxes and SL coupling
+    dephases; the equilibrium converges on the ground state as Pade terms are added
+    (quanta far above kT).
+  * The paper's water tables (tests/test_oracle_water.py): the printed numbers
+    (tests/golden/paper_water_tables.txt), the stretch fundamental at the paper's
+    diagonal peak, three- and four-level linear spectra nearly identical.
 """
 import itertools
 import math
